@@ -1,0 +1,69 @@
+"""Oracle post-processing: energy sums and running conductivities (plain numpy).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Units: energies in eV, lengths in nm, times in fs, hbar in eV fs, densities of
+states per eV per nm^2 (spin included), conductivities in units of e^2/h.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import HBAR_EV_FS, jackson, kpm_sum
+
+H_EV_FS = 2.0 * np.pi * HBAR_EV_FS  # Planck constant h, eV fs
+
+
+def energy_grid(gamma0_ev: float = 2.7, n_e: int = 201) -> np.ndarray:
+    """Reading: n_e energies uniform in [-3 gamma0, 3 gamma0] eV, ends included."""
+    return np.linspace(-3.0 * gamma0_ev, 3.0 * gamma0_ev, n_e)
+
+
+def kpm_density(mu, energies_ev, emax_ev: float, area_nm2: float) -> np.ndarray:
+    """Eqs. (29)-(31): 2/(pi Omega sqrt(1-E~^2)) sum_n g_n (2-delta_n0) T_n(E~) Re mu_n,
+    with E~ = E / E_max, converted to per-eV by the Jacobian 1/E_max.
+
+    ``mu`` is [..., M] (moments averaged over random vectors); returns [..., n_E].
+    """
+    mu = np.asarray(mu)
+    lead = mu.shape[:-1]
+    m = mu.shape[-1]
+    g = jackson(m)
+    e = np.asarray(energies_ev) / emax_ev
+    flat = np.real(mu).reshape(-1, m)
+    out = np.stack([kpm_sum(row, e, g) for row in flat])
+    return (out / (area_nm2 * emax_ev)).reshape(*lead, len(e))
+
+
+def time_grid(n_times: int, dt_hbar_over_gamma0: float, gamma0_ev: float = 2.7) -> np.ndarray:
+    """t_m = m dt in fs, dt given in units of hbar / gamma0."""
+    return np.arange(n_times) * dt_hbar_over_gamma0 * HBAR_EV_FS / gamma0_ev
+
+
+def sigma_gk(rho_cvv: np.ndarray, t_fs: np.ndarray) -> np.ndarray:
+    """Green-Kubo running conductivity, Eq. (6): sigma = e^2 int_0^t rho C_vv dt'.
+
+    ``rho_cvv`` is [N_c, n_E] in nm^2 fs^-2 / (eV nm^2).  Reading: trapezoid rule on
+    the t_m grid.  Returns [N_c, n_E] in e^2/h.
+    """
+    out = np.zeros_like(rho_cvv)
+    for m in range(1, len(t_fs)):
+        out[m] = out[m - 1] + 0.5 * (t_fs[m] - t_fs[m - 1]) * (rho_cvv[m] + rho_cvv[m - 1])
+    return H_EV_FS * out
+
+
+def sigma_e1(rho_dx2: np.ndarray, t_fs: np.ndarray) -> np.ndarray:
+    """Einstein running conductivity, Eq. (9): sigma = e^2 d(rho DX^2)/(2 dt).
+
+    Reading: central differences inside, one-sided differences at both ends."""
+    d = np.gradient(rho_dx2, t_fs, axis=0, edge_order=1)
+    return H_EV_FS * 0.5 * d
+
+
+def sigma_e2(rho_dx2: np.ndarray, t_fs: np.ndarray) -> np.ndarray:
+    """Division-based Einstein conductivity, Eq. (11): e^2 rho DX^2 / (2 t); 0 at t = 0."""
+    out = np.zeros_like(rho_dx2)
+    t = np.asarray(t_fs)
+    nz = t > 0
+    out[nz] = rho_dx2[nz] / (2.0 * t[nz, None])
+    return H_EV_FS * out
