@@ -1,0 +1,219 @@
+/*
+ * kg.h -- C ABI of the GB300 library for linear-scaling Kubo-Greenwood quantum
+ * transport (Fan, Uppstu, Siro and Harju, arXiv 1307.0288).
+ *
+ * The library evaluates, on one GB300 GPU (sm_103a), the Chebyshev recursion
+ * T_{n+1}(H~) = 2 H~ T_n(H~) - T_{n-1}(H~) (Eq. 38) applied to complex vectors through
+ * the nearest-neighbour graphene tight-binding Hamiltonian (Eq. 13), and from it
+ *   - the Chebyshev (KPM) moments C_n = <phi_L|T_n(H~)|phi_R> (Eq. 46, Algorithm 5),
+ *   - the Chebyshev-Bessel propagator U(+-dt) and commutator [X, U(dt)]
+ *     (Eqs. 36-37, Algorithms 6-7),
+ *   - the velocity auto-correlation (VAC) and mean-square-displacement (MSD)
+ *     moments per correlation time (Eqs. 33-34, 42-44, Algorithms 2-3),
+ * plus the host-side energy sums and running conductivities (Eqs. 6, 9, 11, 29-31, 35).
+ *
+ * Conventions for every entry point:
+ *   - Complex vectors are arrays of (re, im) double pairs.  A block of R vectors over
+ *     N sites is laid out [N][R][2] (site-major, vector-minor).
+ *   - A pointer argument named "host or device" may point to host memory or to CUDA
+ *     device memory of the Hamiltonian's device; the library detects which.  The
+ *     library never takes ownership of caller buffers and never keeps a pointer to
+ *     them after the call returns.
+ *   - Every call is synchronous: when it returns, outputs are complete.
+ *   - No exception crosses the ABI.  A negative kg_status is an error; kg_last_error()
+ *     then returns a message (per calling thread).  After KG_ECUDA the CUDA context
+ *     may be unusable; destroy the handle.
+ *   - There is no CPU fallback: without a usable CUDA device every GPU entry point
+ *     returns KG_ENODEV.
+ *
+ * Units: energies eV, lengths nm, times fs (time steps are given in units of
+ * hbar/gamma0), hbar = 0.6582119569 eV fs, velocities nm/fs.
+ */
+#ifndef KG_H
+#define KG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int kg_status;
+#define KG_OK 0
+#define KG_EINVAL (-1)    /* invalid argument (message says which) */
+#define KG_ENOMEM (-2)    /* device or host allocation failed */
+#define KG_ECUDA (-3)     /* a CUDA call failed */
+#define KG_ETIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define KG_ENUMERIC (-5)  /* NaN or Inf found in results */
+#define KG_ENODEV (-6)    /* no usable CUDA device */
+
+/* Message for the last error on the calling thread ("" if none). */
+const char* kg_last_error(void);
+
+/* ABI version of this header (increments on incompatible change). */
+#define KG_ABI_VERSION 1
+int kg_abi_version(void);
+
+/* ------------------------------------------------------------------------- */
+/* Lattice and Hamiltonian (Sec. 2)                                           */
+/* ------------------------------------------------------------------------- */
+
+#define KG_SHEET 0  /* 2D graphene, periodic in x and y, transport along x (zigzag)  */
+#define KG_ZGNR 1   /* zigzag ribbon, periodic in x, open in y, transport along x     */
+#define KG_AGNR 2   /* armchair ribbon, periodic in y, open in x, transport along y   */
+
+/* Sample geometry (Sec. 2): nx dimer lines along the zigzag direction, ny zigzag
+ * chains; N = nx * ny carbon sites, site (i, j) numbered n = j * nx + i.  Position
+ * x = i sqrt(3) a / 2, y = j 3a/2 + (a/2 when i + j is odd).  Periodic directions
+ * need an even extent >= 4.  H = -gamma0 sum_<mn> |m><n| (Eq. 13) plus optional
+ * on-site energies; the library works with H~ = H / emax_ev, so emax_ev must bound
+ * the spectrum (|E| < emax_ev), e.g. 1.05 (3 gamma0 + W/2) for Anderson width W. */
+typedef struct {
+    int32_t kind;       /* KG_SHEET, KG_ZGNR or KG_AGNR */
+    int32_t reserved;   /* must be 0 */
+    int64_t nx;         /* N_x */
+    int64_t ny;         /* N_y */
+    double gamma0_ev;   /* hopping gamma0 (2.7 in the paper) */
+    double bond_nm;     /* carbon-carbon distance a (0.142 in the paper) */
+    double emax_ev;     /* spectral scale E_max > 0 */
+} kg_lattice;
+
+typedef struct kg_hamiltonian kg_hamiltonian;
+
+/* Builds H~ on the current CUDA device and keeps it there (owned by the handle).
+ *   vacancies   host, n_vacancies distinct site numbers in [0, N) of removed atoms
+ *               (Sec. 2, random single vacancies); may be NULL when n_vacancies = 0.
+ *               A removed atom keeps no bonds and carries no amplitude.
+ *   onsite_ev   host [N] on-site energies eps_n in eV (Anderson disorder), or NULL.
+ *   cuda_stream cudaStream_t every later call on this handle is issued on (NULL =
+ *               the legacy default stream).
+ *   out         receives the handle; free it with kg_destroy_hamiltonian.
+ * Errors: KG_EINVAL (bad sizes, duplicate or out-of-range vacancy, |eps| or
+ * 3 gamma0 + max|eps| not below emax_ev), KG_ENOMEM, KG_ECUDA, KG_ENODEV. */
+kg_status kg_build_hamiltonian(const kg_lattice* lattice, const int64_t* vacancies,
+                               int64_t n_vacancies, const double* onsite_ev,
+                               void* cuda_stream, kg_hamiltonian** out);
+
+/* Sizes of a built Hamiltonian: N, N - N_v, E_max, and Omega = L_x L_y in nm^2. */
+kg_status kg_hamiltonian_info(const kg_hamiltonian* h, int64_t* n_sites, int64_t* n_active,
+                              double* emax_ev, double* area_nm2);
+
+/* Releases the handle and all device memory it owns.  NULL is ignored. */
+void kg_destroy_hamiltonian(kg_hamiltonian* h);
+
+/* Host-only (no GPU needed): the neighbour list the library builds for a lattice, as
+ * the paper's NL_nk table (Sec. 3.2, Algorithm 8) in slot-major order: idx_out[k*N + n]
+ * is neighbour k of site n, or -1 if absent (open edge or removed atom).  Slot 0 is
+ * (i-1, j), slot 1 is (i+1, j), slot 2 the bond to the neighbouring chain.  idx_out is
+ * host [3][N] int32, caller-owned. */
+kg_status kg_lattice_neighbors(const kg_lattice* lattice, const int64_t* vacancies,
+                               int64_t n_vacancies, int32_t* idx_out);
+
+/* ------------------------------------------------------------------------- */
+/* Moments and time evolution on the GPU                                      */
+/* ------------------------------------------------------------------------- */
+
+#define KG_FP64 0   /* complex128 vectors, FP64 arithmetic and moment sums */
+#define KG_C64 1    /* complex64 vectors, FP32 recursion, compensated sums combined in FP64 */
+
+typedef struct {
+    int32_t n_moments;   /* M >= 1: moments C_0 .. C_{M-1} (Eqs. 32-34) */
+    int32_t n_vectors;   /* R: random vectors processed together, 1..64 (power of 2) */
+    int32_t n_times;     /* N_c >= 1: correlation times t_m = m dt, m = 0..N_c-1 */
+    int32_t precision;   /* KG_FP64 or KG_C64 */
+    double dt;           /* correlation time step, units of hbar / gamma0 */
+    double bessel_tol;   /* truncation of Eqs. 36-37: first omitted |J_m| < tol (1e-15) */
+} kg_run;
+
+/* DOS moments C_n^DOS = <phi|T_n(H~)|phi> (Eq. 32, Algorithm 5) for each of the R
+ * vectors.  phi: host or device [N][R][2] (Sec. 3.1.1: random vectors with
+ * <phi|phi> = N - N_v, zero on removed atoms).  mu_out: host or device [R][M][2],
+ * caller-owned.  Uses run->n_moments, n_vectors, precision. */
+kg_status kg_dos_moments(kg_hamiltonian* h, const kg_run* run, const double* phi,
+                         double* mu_out);
+
+/* VAC moments C_n^VAC(t_m) = <phi_L|T_n(H~)|phi_R> with |phi_L> = V U^dagger(t_m)|phi>,
+ * |phi_R> = U^dagger(t_m) V |phi> (Eq. 33, Algorithm 2), t_m = m dt, advanced with
+ * Eqs. 42-43.  V = (i/hbar)[H, X] (Eq. 15), so the moments are in (nm/fs)^2.
+ * phi: host or device [N][R][2].  mu_out: host or device [R][N_c][M][2]. */
+kg_status kg_vac(kg_hamiltonian* h, const kg_run* run, const double* phi, double* mu_out);
+
+/* MSD moments C_n^MSD(t_m) = <phi_L|T_n(H~)|phi_L> with |phi_L> = [X, U(t_m)]|phi>
+ * (Eq. 34, Algorithm 3), advanced with Eq. 44; in nm^2.  C^MSD(t_0) = 0.
+ * phi: host or device [N][R][2].  mu_out: host or device [R][N_c][M][2]. */
+kg_status kg_msd(kg_hamiltonian* h, const kg_run* run, const double* phi, double* mu_out);
+
+#define KG_OP_H 0    /* out = H~ in                                  (Algorithm 8) */
+#define KG_OP_XH 1   /* out = [X, H~] in, (X_n - X_m) H~_nm, in nm    (Eq. 15)     */
+#define KG_OP_V 2    /* out = V in = (i/hbar)[H, X] in, in nm/fs      (Eq. 15)     */
+
+/* One sparse product on R vectors.  in, out: device [N][R][2] (distinct buffers). */
+kg_status kg_apply(kg_hamiltonian* h, int op, const double* in_dev, double* out_dev,
+                   int n_vectors);
+
+#define KG_U_FORWARD 0    /* out = U(+dt) in = exp(-i H dt / hbar) in  (Eq. 36, Algorithm 6) */
+#define KG_U_BACKWARD 1   /* out = U(-dt) in = U(dt)^dagger in         (Eq. 36, Algorithm 6) */
+#define KG_U_COMMUTATOR 2 /* out = [X, U(dt)] in, in nm                (Eq. 37, Algorithm 7) */
+
+/* One Chebyshev-Bessel time step of length dt (units of hbar/gamma0) on R vectors.
+ * in, out: device [N][R][2] (distinct buffers). */
+kg_status kg_evolve(kg_hamiltonian* h, double dt, int which, double bessel_tol,
+                    const double* in_dev, double* out_dev, int n_vectors);
+
+/* ------------------------------------------------------------------------- */
+/* Timing counters (filled by the GPU entry points above)                    */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    double kpm_ms;          /* CUDA-event time of the moment recursions (Algorithm 5) */
+    double evolve_ms;       /* CUDA-event time of the time-evolution steps (Algorithms 6-7) */
+    int64_t kpm_launches;   /* fused moment-step kernel launches */
+    int64_t evolve_launches;/* fused evolution-step kernel launches */
+    int64_t other_launches; /* every other kernel launched (copies, V, reductions) */
+    double kpm_site_steps;  /* site x vector x recursion-step updates in the moment loops */
+    double evolve_site_steps;/* same for the evolution loops (all chains) */
+} kg_timing;
+
+/* Enables (1) or disables (0) CUDA-event timing of the phases; resets the counters. */
+kg_status kg_timing_enable(kg_hamiltonian* h, int enable);
+/* Reads the counters accumulated since the last kg_timing_enable (synchronises). */
+kg_status kg_timing_read(kg_hamiltonian* h, kg_timing* out);
+
+/* ------------------------------------------------------------------------- */
+/* Host-side helpers (FP64, no GPU needed)                                    */
+/* ------------------------------------------------------------------------- */
+
+/* J_m(tau), m = 0..n_terms-1, of the series Eqs. 36-37, with n_terms = the smallest
+ * m > tau with |J_m(tau)| < tol (evaluated by Bessel's integral, A&S 9.1.21, with the
+ * periodic trapezoidal rule).  j_out: host, capacity max_terms.  Returns KG_EINVAL if
+ * max_terms is too small. */
+kg_status kg_bessel_series(double tau, double tol, int max_terms, double* j_out,
+                           int* n_terms);
+
+/* Jackson damping g_n, n < M (Eq. 35).  g_out: host [M]. */
+kg_status kg_jackson(int n_moments, double* g_out);
+
+/* Chebyshev sum of Eqs. 29-31 on physical energies:
+ *   out[s][e] = 2 / (pi Omega E_max sqrt(1 - E~^2)) sum_n g_n (2 - delta_n0) T_n(E~) mu[s][n],
+ * E~ = energies_ev[e] / emax_ev (|E~| < 1), g_n Jackson (Eq. 35).  mu: host [n_sets][M]
+ * (real parts of the moments, averaged over random vectors); out: host [n_sets][n_e]
+ * in 1/(eV nm^2) times the moments' unit. */
+kg_status kg_kpm_sum(const double* mu, int n_sets, int n_moments, const double* energies_ev,
+                     int n_e, double emax_ev, double area_nm2, double* out);
+
+#define KG_SIGMA_GK 0   /* Eq. 6: e^2 int_0^t rho C_vv dt' (trapezoid)            */
+#define KG_SIGMA_E1 1   /* Eq. 9: e^2 d(rho DX^2)/(2 dt) (central differences)    */
+#define KG_SIGMA_E2 2   /* Eq. 11: e^2 rho DX^2 / (2 t), 0 at t = 0               */
+
+/* Running conductivity in units of e^2/h on the grid t_m = m dt_fs.
+ *   density: host [N_c][n_e], rho C_vv (for KG_SIGMA_GK, in 1/(eV fs^2)) or
+ *            rho DX^2 (for E1/E2, in 1/eV), e.g. from kg_kpm_sum.
+ *   out:     host [N_c][n_e]. */
+kg_status kg_conductivity(int formula, const double* density, int n_times, int n_e,
+                          double dt_fs, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KG_H */

@@ -1,0 +1,328 @@
+"""Python binding of the GB300 Kubo-Greenwood transport library (``libkg.so``).
+
+Thin ctypes layer over the C ABI declared in ``include/kg.h``: every function here
+has the name of the C entry point without the ``kg_`` prefix and only marshals
+arguments (numpy arrays for host memory, torch CUDA tensors for device memory).
+All computation runs in the library's CUDA kernels or its host C++ code; there is
+no Python or CPU fallback.  If the library cannot be loaded, importing this
+package raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KG_SHEET, KG_ZGNR, KG_AGNR = 0, 1, 2
+KG_FP64, KG_C64 = 0, 1
+KG_OP_H, KG_OP_XH, KG_OP_V = 0, 1, 2
+KG_U_FORWARD, KG_U_BACKWARD, KG_U_COMMUTATOR = 0, 1, 2
+KG_SIGMA_GK, KG_SIGMA_E1, KG_SIGMA_E2 = 0, 1, 2
+HBAR_EV_FS = 0.6582119569
+
+_STATUS = {0: "KG_OK", -1: "KG_EINVAL", -2: "KG_ENOMEM", -3: "KG_ECUDA", -4: "KG_ETIMEOUT",
+           -5: "KG_ENUMERIC", -6: "KG_ENODEV"}
+
+
+class KgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Lattice(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("nx", ctypes.c_int64),
+                ("ny", ctypes.c_int64), ("gamma0_ev", ctypes.c_double),
+                ("bond_nm", ctypes.c_double), ("emax_ev", ctypes.c_double)]
+
+
+class _Run(ctypes.Structure):
+    _fields_ = [("n_moments", ctypes.c_int32), ("n_vectors", ctypes.c_int32),
+                ("n_times", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("dt", ctypes.c_double), ("bessel_tol", ctypes.c_double)]
+
+
+class _Timing(ctypes.Structure):
+    _fields_ = [("kpm_ms", ctypes.c_double), ("evolve_ms", ctypes.c_double),
+                ("kpm_launches", ctypes.c_int64), ("evolve_launches", ctypes.c_int64),
+                ("other_launches", ctypes.c_int64), ("kpm_site_steps", ctypes.c_double),
+                ("evolve_site_steps", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+# (name, restype, argtypes) of every exported entry point of include/kg.h
+ABI = [
+    ("kg_last_error", ctypes.c_char_p, []),
+    ("kg_abi_version", _I, []),
+    ("kg_build_hamiltonian", _I, [ctypes.POINTER(_Lattice), _P, _I64, _P, _P, ctypes.POINTER(_P)]),
+    ("kg_hamiltonian_info", _I, [_P, _P, _P, _P, _P]),
+    ("kg_destroy_hamiltonian", None, [_P]),
+    ("kg_lattice_neighbors", _I, [ctypes.POINTER(_Lattice), _P, _I64, _P]),
+    ("kg_dos_moments", _I, [_P, ctypes.POINTER(_Run), _P, _P]),
+    ("kg_vac", _I, [_P, ctypes.POINTER(_Run), _P, _P]),
+    ("kg_msd", _I, [_P, ctypes.POINTER(_Run), _P, _P]),
+    ("kg_apply", _I, [_P, _I, _P, _P, _I]),
+    ("kg_evolve", _I, [_P, _D, _I, _D, _P, _P, _I]),
+    ("kg_timing_enable", _I, [_P, _I]),
+    ("kg_timing_read", _I, [_P, ctypes.POINTER(_Timing)]),
+    ("kg_bessel_series", _I, [_D, _D, _I, _P, ctypes.POINTER(_I)]),
+    ("kg_jackson", _I, [_I, _P]),
+    ("kg_kpm_sum", _I, [_P, _I, _I, _P, _I, _D, _D, _P]),
+    ("kg_conductivity", _I, [_I, _P, _I, _I, _D, _P]),
+]
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads ``libkg.so`` (building it from source first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"libkg.so not found at {path}")
+        L = ctypes.CDLL(path)
+        for name, res, args in ABI:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise KgError(status, lib().kg_last_error().decode())
+
+
+def last_error() -> str:
+    return lib().kg_last_error().decode()
+
+
+def abi_version() -> int:
+    return lib().kg_abi_version()
+
+
+# ----------------------------------------------------------------- pointer marshalling
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype=None, shape=None, writable=False):
+    """(address, keep-alive object) of a numpy array or torch tensor."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), x
+    a = np.asarray(x)
+    if dtype is not None and a.dtype != dtype:
+        if writable:
+            raise ValueError(f"output array must have dtype {dtype}")
+        a = a.astype(dtype)
+    if not a.flags["C_CONTIGUOUS"]:
+        if writable:
+            raise ValueError("output array must be C-contiguous")
+        a = np.ascontiguousarray(a)
+    if shape is not None and a.size != int(np.prod(shape)):
+        raise ValueError(f"array has {a.size} elements, expected {int(np.prod(shape))}")
+    return a.ctypes.data, a
+
+
+def _lattice(kind, nx, ny, gamma0_ev, bond_nm, emax_ev) -> _Lattice:
+    return _Lattice(int(kind), 0, int(nx), int(ny), float(gamma0_ev), float(bond_nm), float(emax_ev))
+
+
+# ----------------------------------------------------------------- Hamiltonian
+
+class Hamiltonian:
+    """Owns a ``kg_hamiltonian*`` (device-resident H~)."""
+
+    def __init__(self, handle: int, kind: int, nx: int, ny: int):
+        self._h = ctypes.c_void_p(handle)
+        self.kind, self.nx, self.ny = kind, nx, ny
+        n, na, emax, area = (ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double(),
+                             ctypes.c_double())
+        _check(lib().kg_hamiltonian_info(self._h, ctypes.byref(n), ctypes.byref(na),
+                                         ctypes.byref(emax), ctypes.byref(area)))
+        self.n, self.n_active, self.emax_ev, self.area_nm2 = n.value, na.value, emax.value, area.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().kg_destroy_hamiltonian(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_hamiltonian(kind: int, nx: int, ny: int, *, emax_ev: float, vacancies=None,
+                      onsite_ev=None, gamma0_ev: float = 2.7, bond_nm: float = 0.142,
+                      stream=None) -> Hamiltonian:
+    """kg_build_hamiltonian.  ``stream``: a torch.cuda.Stream, a raw cudaStream_t, or None."""
+    lat = _lattice(kind, nx, ny, gamma0_ev, bond_nm, emax_ev)
+    vac = np.zeros(0, np.int64) if vacancies is None else np.ascontiguousarray(vacancies, np.int64)
+    on = None if onsite_ev is None else np.ascontiguousarray(onsite_ev, np.float64)
+    s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    out = ctypes.c_void_p()
+    _check(lib().kg_build_hamiltonian(ctypes.byref(lat), vac.ctypes.data if len(vac) else None,
+                                      len(vac), None if on is None else on.ctypes.data,
+                                      ctypes.c_void_p(s), ctypes.byref(out)))
+    return Hamiltonian(out.value, kind, nx, ny)
+
+
+def from_workload(w, stream=None) -> Hamiltonian:
+    """Hamiltonian of a ``kg_inputs.Workload``."""
+    return build_hamiltonian(w.kind, w.nx, w.ny, emax_ev=w.emax_ev, vacancies=w.vacancies,
+                             onsite_ev=w.onsite, gamma0_ev=w.gamma0_ev, bond_nm=w.bond_nm,
+                             stream=stream)
+
+
+def lattice_neighbors(kind: int, nx: int, ny: int, vacancies=None, *, gamma0_ev=2.7,
+                      bond_nm=0.142, emax_ev=8.505) -> np.ndarray:
+    """kg_lattice_neighbors (host only): int32 [3][N], -1 where absent."""
+    lat = _lattice(kind, nx, ny, gamma0_ev, bond_nm, emax_ev)
+    vac = np.zeros(0, np.int64) if vacancies is None else np.ascontiguousarray(vacancies, np.int64)
+    out = np.empty((3, nx * ny), dtype=np.int32)
+    _check(lib().kg_lattice_neighbors(ctypes.byref(lat), vac.ctypes.data if len(vac) else None,
+                                      len(vac), out.ctypes.data))
+    return out
+
+
+# ----------------------------------------------------------------- moments
+
+def _run(n_moments, n_vectors, n_times=1, precision=KG_FP64, dt=1.0, bessel_tol=1e-15) -> _Run:
+    return _Run(int(n_moments), int(n_vectors), int(n_times), int(precision), float(dt),
+                float(bessel_tol))
+
+
+def _nvec(phi, n):
+    shape = tuple(phi.shape)
+    if len(shape) == 1:
+        return 1
+    if len(shape) == 2 and shape[0] == n:
+        return int(shape[1])
+    raise ValueError(f"phi must be [N] or [N][R] complex with N = {n}")
+
+
+def _complex_in(phi):
+    if _is_torch(phi):
+        import torch
+        if phi.dtype != torch.complex128:
+            raise ValueError("device phi must be complex128")
+        return _ptr(phi)
+    return _ptr(np.ascontiguousarray(phi, dtype=np.complex128))
+
+
+def _moments_call(fn, h: Hamiltonian, phi, run: _Run, shape, out):
+    pp, keep = _complex_in(phi)
+    if out is None:
+        res = np.zeros(shape, dtype=np.complex128)
+        op, keep_o = res.ctypes.data, res
+    else:
+        op, keep_o = _ptr(out, writable=True)
+        res = out
+    _check(fn(h.handle, ctypes.byref(run), ctypes.c_void_p(pp), ctypes.c_void_p(op)))
+    return res
+
+
+def dos_moments(h: Hamiltonian, phi, n_moments: int, precision: int = KG_FP64, out=None):
+    """kg_dos_moments -> complex [R][M] (numpy, or ``out`` if given)."""
+    r = _nvec(phi, h.n)
+    run = _run(n_moments, r, 1, precision)
+    return _moments_call(lib().kg_dos_moments, h, phi, run, (r, n_moments), out)
+
+
+def vac(h: Hamiltonian, phi, n_moments: int, n_times: int, dt: float, *, bessel_tol=1e-15,
+        precision: int = KG_FP64, out=None):
+    """kg_vac -> complex [R][N_c][M]."""
+    r = _nvec(phi, h.n)
+    run = _run(n_moments, r, n_times, precision, dt, bessel_tol)
+    return _moments_call(lib().kg_vac, h, phi, run, (r, n_times, n_moments), out)
+
+
+def msd(h: Hamiltonian, phi, n_moments: int, n_times: int, dt: float, *, bessel_tol=1e-15,
+        precision: int = KG_FP64, out=None):
+    """kg_msd -> complex [R][N_c][M]."""
+    r = _nvec(phi, h.n)
+    run = _run(n_moments, r, n_times, precision, dt, bessel_tol)
+    return _moments_call(lib().kg_msd, h, phi, run, (r, n_times, n_moments), out)
+
+
+def apply(h: Hamiltonian, op: int, x, out):
+    """kg_apply on device tensors x, out (complex128 [N] or [N][R])."""
+    r = _nvec(x, h.n)
+    _check(lib().kg_apply(h.handle, int(op), ctypes.c_void_p(x.data_ptr()),
+                          ctypes.c_void_p(out.data_ptr()), r))
+    return out
+
+
+def evolve(h: Hamiltonian, dt: float, which: int, x, out, bessel_tol: float = 1e-15):
+    """kg_evolve on device tensors x, out (complex128 [N] or [N][R])."""
+    r = _nvec(x, h.n)
+    _check(lib().kg_evolve(h.handle, float(dt), int(which), float(bessel_tol),
+                           ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), r))
+    return out
+
+
+def timing_enable(h: Hamiltonian, enable: bool = True):
+    _check(lib().kg_timing_enable(h.handle, 1 if enable else 0))
+
+
+def timing_read(h: Hamiltonian) -> dict:
+    t = _Timing()
+    _check(lib().kg_timing_read(h.handle, ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in _Timing._fields_}
+
+
+# ----------------------------------------------------------------- host helpers
+
+def bessel_series(tau: float, tol: float = 1e-15, max_terms: int = 1000) -> np.ndarray:
+    """kg_bessel_series -> J_m(tau), m < N_p."""
+    j = np.zeros(max_terms)
+    n = ctypes.c_int()
+    _check(lib().kg_bessel_series(float(tau), float(tol), max_terms, j.ctypes.data, ctypes.byref(n)))
+    return j[:n.value].copy()
+
+
+def jackson(n_moments: int) -> np.ndarray:
+    g = np.zeros(n_moments)
+    _check(lib().kg_jackson(int(n_moments), g.ctypes.data))
+    return g
+
+
+def kpm_sum(mu, energies_ev, emax_ev: float, area_nm2: float) -> np.ndarray:
+    """kg_kpm_sum: mu real [..., M] -> [..., n_E] (Eqs. 29-31)."""
+    mu = np.ascontiguousarray(np.real(mu), dtype=np.float64)
+    lead, m = mu.shape[:-1], mu.shape[-1]
+    e = np.ascontiguousarray(energies_ev, dtype=np.float64)
+    sets = int(np.prod(lead)) if lead else 1
+    out = np.zeros((sets, len(e)))
+    _check(lib().kg_kpm_sum(mu.ctypes.data, sets, m, e.ctypes.data, len(e), float(emax_ev),
+                            float(area_nm2), out.ctypes.data))
+    return out.reshape(*lead, len(e))
+
+
+def conductivity(formula: int, density, dt_fs: float) -> np.ndarray:
+    """kg_conductivity: density [N_c][n_E] -> sigma [N_c][n_E] in e^2/h."""
+    d = np.ascontiguousarray(density, dtype=np.float64)
+    out = np.zeros_like(d)
+    _check(lib().kg_conductivity(int(formula), d.ctypes.data, d.shape[0], d.shape[1],
+                                 float(dt_fs), out.ctypes.data))
+    return out

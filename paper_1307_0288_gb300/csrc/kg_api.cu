@@ -1,0 +1,582 @@
+// GPU entry points of the C ABI: Hamiltonian handle, workspace, and the moment and
+// time-evolution drivers (Algorithms 2, 3, 5, 6, 7 of the paper).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kg_internal.h"
+
+namespace kg {
+
+// Device buffer owned by the handle.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // Grows to at least `want` bytes; new memory is zero-filled (the zero row of every
+    // vector block relies on it).
+    kg_status ensure(size_t want, cudaStream_t s) {
+        if (bytes >= want) return KG_OK;
+        release();
+        if (cudaMalloc(&p, want) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return fail(KG_ENOMEM, "cudaMalloc of " + std::to_string(want) + " bytes failed");
+        }
+        bytes = want;
+        KG_CUDA_TRY(cudaMemsetAsync(p, 0, want, s));
+        return KG_OK;
+    }
+};
+
+struct TimedPhase {
+    cudaEvent_t a, b;
+    int kind;   // 0 kpm, 1 evolve
+};
+
+}  // namespace kg
+
+struct kg_hamiltonian {
+    int kind = 0;
+    int64_t nx = 0, ny = 0, n = 0, n_active = 0;
+    double gamma0 = 0, bond = 0, emax = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    kg::DevBuf idx, onsite, parity;
+    kg::DevH dev;
+    // workspace
+    static constexpr int kNumVec = 10;
+    kg::DevBuf vec[kNumVec];
+    kg::DevBuf part_first, part_ring, moments;
+    // timing
+    bool timing = false;
+    std::vector<kg::TimedPhase> phases;
+    std::vector<cudaEvent_t> spare_events;
+    kg_timing counters{};
+};
+
+namespace kg {
+
+static constexpr int kRing = 256;   // partial-sum slabs reduced per launch
+
+static kg_status check_device(kg_hamiltonian* h) {
+    int cur = -1;
+    KG_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != h->device) KG_CUDA_TRY(cudaSetDevice(h->device));
+    return KG_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static bool valid_r(int r) { return r >= 1 && r <= 64 && (r & (r - 1)) == 0; }
+
+static cudaEvent_t take_event(kg_hamiltonian* h) {
+    if (!h->spare_events.empty()) {
+        cudaEvent_t e = h->spare_events.back();
+        h->spare_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct PhaseTimer {
+    kg_hamiltonian* h;
+    int kind;
+    cudaEvent_t a = nullptr;
+    PhaseTimer(kg_hamiltonian* h_, int kind_) : h(h_), kind(kind_) {
+        if (h->timing) {
+            a = take_event(h);
+            cudaEventRecord(a, h->stream);
+        }
+    }
+    ~PhaseTimer() {
+        if (h->timing && a) {
+            cudaEvent_t b = take_event(h);
+            cudaEventRecord(b, h->stream);
+            h->phases.push_back({a, b, kind});
+        }
+    }
+};
+
+static size_t vec_bytes(const kg_hamiltonian* h, int R) {
+    return (size_t)(h->n + 1) * (size_t)R * sizeof(double2);
+}
+
+// Makes `count` vector blocks of R columns available.  Row n of every block (the
+// zero row that absent neighbours point at) is cleared on each call, since a block
+// may have been used with another R before.
+static kg_status ensure_vectors(kg_hamiltonian* h, int R, int count) {
+    if (count > kg_hamiltonian::kNumVec) return fail(KG_EINVAL, "internal: too many vectors");
+    const size_t want = vec_bytes(h, R);
+    for (int k = 0; k < count; k++) {
+        KG_TRY(h->vec[k].ensure(want, h->stream));
+        KG_CUDA_TRY(cudaMemsetAsync((char*)h->vec[k].p + (size_t)h->n * R * sizeof(double2), 0,
+                                    (size_t)R * sizeof(double2), h->stream));
+    }
+    return KG_OK;
+}
+
+static double2* V(kg_hamiltonian* h, int k) { return (double2*)h->vec[k].p; }
+
+// Copies N rows of R vectors from a host or device source into a device block.
+static kg_status copy_in(kg_hamiltonian* h, const double* src, double2* dst, int R) {
+    const size_t bytes = (size_t)h->n * R * sizeof(double2);
+    KG_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes,
+                                is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                h->stream));
+    return KG_OK;
+}
+
+static kg_status copy_out(kg_hamiltonian* h, const void* src, double* dst, size_t bytes) {
+    KG_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes,
+                                is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                h->stream));
+    KG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return KG_OK;
+}
+
+static kg_status ensure_partials(kg_hamiltonian* h, int R, int grid) {
+    KG_TRY(h->part_first.ensure((size_t)grid * R * 4 * sizeof(double), h->stream));
+    KG_TRY(h->part_ring.ensure((size_t)kRing * grid * R * 2 * sizeof(double), h->stream));
+    return KG_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// KPM moments (Algorithm 5) of one pair (phi_L, phi_R) block of R vectors.
+//   sym: phi_L == phi_R, two moments per recursion step (Chebyshev doubling)
+//   buffers b0, b1: scratch vector blocks; phi_r is not modified.
+//   mu: device [R][r_stride] double2, moments written at mu[r*r_stride + n], n < M.
+// ---------------------------------------------------------------------------------
+static kg_status kpm_moments(kg_hamiltonian* h, int R, int M, bool sym, const double2* phi_l,
+                             const double2* phi_r, double2* b0, double2* b1, double2* mu,
+                             int64_t r_stride) {
+    PhaseTimer t(h, 0);
+    const int grid = stream_grid(h->n * R);
+    KG_TRY(ensure_partials(h, R, grid));
+    double* pf = (double*)h->part_first.p;
+    double* ring = (double*)h->part_ring.p;
+    cudaStream_t s = h->stream;
+    // first step: phi_1 = H~ phi_0 (into b1), moments 0 and 1
+    if (sym) KG_CUDA_TRY(launch_kpm_sym(h->dev, R, true, phi_r, nullptr, b1, pf, grid, s));
+    else KG_CUDA_TRY(launch_kpm_gen(h->dev, R, true, phi_l, phi_r, nullptr, b1, pf, grid, s));
+    KG_CUDA_TRY(launch_reduce_first(pf, grid, R, sym, mu, r_stride, M, s));
+    h->counters.kpm_launches += 1;
+    h->counters.other_launches += 1;
+    h->counters.kpm_site_steps += (double)h->n * R;
+    // remaining steps n = 1..S: phi_{n+1} = 2H~phi_n - phi_{n-1}
+    const int steps = sym ? (M - 1) / 2 : M - 2;
+    const double2* cur = b1;
+    const double2* prev = phi_r;
+    double2* out = b0;
+    int pending = 0, first_pending = 1;
+    for (int n = 1; n <= steps; n++) {
+        double* slab = ring + (int64_t)((n - 1) % kRing) * grid * R * 2;
+        if (sym) KG_CUDA_TRY(launch_kpm_sym(h->dev, R, false, cur, prev, out, slab, grid, s));
+        else KG_CUDA_TRY(launch_kpm_gen(h->dev, R, false, phi_l, cur, prev, out, slab, grid, s));
+        h->counters.kpm_launches += 1;
+        h->counters.kpm_site_steps += (double)h->n * R;
+        pending++;
+        if (pending == kRing || n == steps) {
+            KG_CUDA_TRY(launch_reduce_ring(ring, (first_pending - 1) % kRing, pending, kRing, grid, R,
+                                           sym, first_pending, mu, r_stride, M, s));
+            h->counters.other_launches += 1;
+            first_pending = n + 1;
+            pending = 0;
+        }
+        // rotate: the new phi_n is `out`; phi_{n-1} becomes the next output (in place)
+        const double2* new_cur = out;
+        prev = cur;
+        out = const_cast<double2*>(cur);
+        cur = new_cur;
+    }
+    return KG_OK;
+}
+
+// Bessel coefficients of one time step and the (s i)^m phase factors (Eq. 36).
+struct Series {
+    std::vector<double> j;
+    int np = 0;
+};
+
+static kg_status series_for(kg_hamiltonian* h, double dt, double tol, Series* out) {
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(KG_EINVAL, "dt must be positive");
+    if (!(tol > 0) || !(tol < 1)) return fail(KG_EINVAL, "bessel_tol must be in (0, 1)");
+    const double tau = h->emax * dt / h->gamma0;   // tau = E_max dt / hbar, dt in hbar/gamma0
+    const int cap = (int)tau + 400;
+    out->j.assign((size_t)cap, 0.0);
+    KG_TRY(bessel_series(tau, tol, cap, out->j.data(), &out->np));
+    return KG_OK;
+}
+
+// 2 J_m (s i)^m as (cr, ci); s = -1 for U(+dt), +1 for U(-dt).
+static void term_coef(const Series& ser, int m, int s, double* cr, double* ci) {
+    const double f = 2.0 * ser.j[(size_t)m];
+    switch (m & 3) {
+        case 0: *cr = f; *ci = 0; break;
+        case 1: *cr = 0; *ci = f * s; break;
+        case 2: *cr = -f; *ci = 0; break;
+        default: *cr = 0; *ci = -f * s; break;
+    }
+}
+
+// Runs the Chebyshev-Bessel series over prepared chains; rotates chain pointers.
+//   chains: nch plain chains with cur = input (p_0), nxt buffers for p_1 given in
+//   p1[k], accumulators acc[k]; xc: commutator chain of the last plain chain with
+//   buffers q1, q0 (q0 receives q_2), routed to qacc (null = acc[0]).
+// The plain-chain inputs are overwritten from m = 2 on (p_m replaces p_{m-2}).
+static kg_status run_series(kg_hamiltonian* h, int R, const Series& ser, int s, int nch, bool xc,
+                            double2* const* in, double2* const* p1, double2* const* acc,
+                            double2* q1, double2* q0, double2* qacc) {
+    PhaseTimer t(h, 1);
+    const int grid = stream_grid(h->n * R);
+    Chains ch;
+    double2* cur[3];
+    double2* prv[3];
+    for (int k = 0; k < nch; k++) {
+        ch.cur[k] = in[k];
+        ch.nxt[k] = p1[k];
+        ch.acc[k] = acc[k];
+        cur[k] = p1[k];
+        prv[k] = in[k];
+    }
+    if (xc) {
+        ch.qnxt = q1;
+        ch.qacc = qacc;
+    }
+    double cr = 0, ci = 0;
+    if (ser.np > 1) term_coef(ser, 1, s, &cr, &ci);
+    // first step: p_1 = H~ p_0, acc = J_0 p_0 + c_1 p_1 (c_1 = 0 when N_p = 1)
+    KG_CUDA_TRY(launch_evolve(h->dev, R, nch, xc, true, ser.j[0], cr, ci, ch, grid, h->stream));
+    h->counters.evolve_launches += 1;
+    h->counters.evolve_site_steps += (double)h->n * R * (nch + (xc ? 1 : 0));
+    double2* qc = q1;
+    double2* qp = nullptr;
+    double2* qn = q0;
+    for (int m = 2; m < ser.np; m++) {
+        term_coef(ser, m, s, &cr, &ci);
+        for (int k = 0; k < nch; k++) {
+            ch.cur[k] = cur[k];
+            ch.prev[k] = prv[k];
+            ch.nxt[k] = prv[k];   // in place: p_m overwrites p_{m-2}
+        }
+        if (xc) {
+            ch.qcur = qc;
+            ch.qprev = qp;
+            ch.qnxt = qn;
+        }
+        KG_CUDA_TRY(launch_evolve(h->dev, R, nch, xc, false, 0.0, cr, ci, ch, grid, h->stream));
+        h->counters.evolve_launches += 1;
+        h->counters.evolve_site_steps += (double)h->n * R * (nch + (xc ? 1 : 0));
+        for (int k = 0; k < nch; k++) {
+            double2* t2 = prv[k];
+            prv[k] = cur[k];
+            cur[k] = t2;
+        }
+        if (xc) {
+            // q_m now sits in qn; q_{m+1} will overwrite q_{m-1}
+            double2* newc = qn;
+            qp = qc;
+            qc = newc;
+            qn = qp;
+        }
+    }
+    return KG_OK;
+}
+
+static kg_status check_run(const kg_hamiltonian* h, const kg_run* run, bool need_time) {
+    if (!h) return fail(KG_EINVAL, "hamiltonian is NULL");
+    if (!run) return fail(KG_EINVAL, "run is NULL");
+    if (run->n_moments < 1) return fail(KG_EINVAL, "n_moments must be >= 1");
+    if (!valid_r(run->n_vectors)) return fail(KG_EINVAL, "n_vectors must be a power of two in 1..64");
+    if (run->precision != KG_FP64 && run->precision != KG_C64) return fail(KG_EINVAL, "unknown precision");
+    if (run->precision == KG_C64) return fail(KG_EINVAL, "precision KG_C64 is not available in this build");
+    if (need_time && run->n_times < 1) return fail(KG_EINVAL, "n_times must be >= 1");
+    return KG_OK;
+}
+
+static kg_status ensure_moments(kg_hamiltonian* h, size_t count) {
+    return h->moments.ensure(count * sizeof(double2), h->stream);
+}
+
+}  // namespace kg
+
+using namespace kg;
+
+extern "C" {
+
+kg_status kg_build_hamiltonian(const kg_lattice* lattice, const int64_t* vacancies,
+                               int64_t n_vacancies, const double* onsite_ev, void* cuda_stream,
+                               kg_hamiltonian** out) {
+    clear_error();
+    if (!out) return fail(KG_EINVAL, "out is NULL");
+    *out = nullptr;
+    HostLattice hl;
+    KG_TRY(build_host_lattice(lattice, vacancies, n_vacancies, &hl));
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return fail(KG_ENODEV, "no CUDA device available");
+    }
+    const int64_t n = hl.n;
+    double max_eps = 0.0;
+    if (onsite_ev) {
+        for (int64_t k = 0; k < n; k++) {
+            if (!std::isfinite(onsite_ev[k])) return fail(KG_EINVAL, "onsite energy not finite");
+            max_eps = std::fmax(max_eps, std::fabs(onsite_ev[k]));
+        }
+    }
+    if (!(3.0 * lattice->gamma0_ev + max_eps < lattice->emax_ev))
+        return fail(KG_EINVAL, "emax_ev must exceed 3 gamma0 + max |eps|");
+    kg_hamiltonian* h = new (std::nothrow) kg_hamiltonian();
+    if (!h) return fail(KG_ENOMEM, "host allocation failed");
+    h->kind = hl.kind;
+    h->nx = hl.nx;
+    h->ny = hl.ny;
+    h->n = n;
+    h->n_active = hl.n_active;
+    h->gamma0 = lattice->gamma0_ev;
+    h->bond = lattice->bond_nm;
+    h->emax = lattice->emax_ev;
+    h->stream = (cudaStream_t)cuda_stream;
+    auto bail = [&](kg_status st) {
+        kg_destroy_hamiltonian(h);
+        return st;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return bail(fail(KG_ENODEV, "cudaGetDevice failed"));
+    // neighbour table with the sentinel pointing at the zero row n
+    std::vector<int32_t> idx(hl.idx.size());
+    for (size_t k = 0; k < idx.size(); k++) idx[k] = hl.idx[k] < 0 ? (int32_t)n : hl.idx[k];
+    kg_status st = h->idx.ensure(idx.size() * sizeof(int32_t), h->stream);
+    if (st != KG_OK) return bail(st);
+    if (cudaMemcpyAsync(h->idx.p, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess)
+        return bail(fail(KG_ECUDA, "upload of the neighbour table failed"));
+    h->dev.idx = (const int32_t*)h->idx.p;
+    h->dev.istride = n;
+    h->dev.n = n;
+    h->dev.h = -lattice->gamma0_ev / lattice->emax_ev;
+    for (int p = 0; p < 2; p++)
+        for (int k = 0; k < 3; k++)
+            h->dev.dh[p][k] = slot_displacement(hl.kind, lattice->bond_nm, p, k) * h->dev.h;
+    h->dev.ytransport = (hl.kind == KG_AGNR);
+    if (onsite_ev) {
+        std::vector<double> e((size_t)n + 1, 0.0);
+        for (int64_t k = 0; k < n; k++) e[(size_t)k] = hl.removed[(size_t)k] ? 0.0 : onsite_ev[k] / lattice->emax_ev;
+        st = h->onsite.ensure(e.size() * sizeof(double), h->stream);
+        if (st != KG_OK) return bail(st);
+        if (cudaMemcpyAsync(h->onsite.p, e.data(), e.size() * sizeof(double), cudaMemcpyHostToDevice,
+                            h->stream) != cudaSuccess)
+            return bail(fail(KG_ECUDA, "upload of on-site energies failed"));
+        h->dev.onsite = (const double*)h->onsite.p;
+    }
+    if (h->dev.ytransport) {
+        st = h->parity.ensure((size_t)n + 1, h->stream);
+        if (st != KG_OK) return bail(st);
+        if (cudaMemcpyAsync(h->parity.p, hl.parity.data(), (size_t)n, cudaMemcpyHostToDevice,
+                            h->stream) != cudaSuccess)
+            return bail(fail(KG_ECUDA, "upload of the parity table failed"));
+        h->dev.parity = (const uint8_t*)h->parity.p;
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return bail(fail(KG_ECUDA, std::string("build: ") + cudaGetErrorString(cudaGetLastError())));
+    *out = h;
+    return KG_OK;
+}
+
+kg_status kg_hamiltonian_info(const kg_hamiltonian* h, int64_t* n_sites, int64_t* n_active,
+                              double* emax_ev, double* area_nm2) {
+    if (!h) return fail(KG_EINVAL, "hamiltonian is NULL");
+    if (n_sites) *n_sites = h->n;
+    if (n_active) *n_active = h->n_active;
+    if (emax_ev) *emax_ev = h->emax;
+    if (area_nm2) *area_nm2 = (std::sqrt(3.0) * h->nx * h->bond / 2.0) * (1.5 * h->ny * h->bond);
+    return KG_OK;
+}
+
+void kg_destroy_hamiltonian(kg_hamiltonian* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    h->idx.release();
+    h->onsite.release();
+    h->parity.release();
+    for (auto& v : h->vec) v.release();
+    h->part_first.release();
+    h->part_ring.release();
+    h->moments.release();
+    for (auto& p : h->phases) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : h->spare_events) cudaEventDestroy(e);
+    delete h;
+}
+
+kg_status kg_dos_moments(kg_hamiltonian* h, const kg_run* run, const double* phi, double* mu_out) {
+    clear_error();
+    KG_TRY(check_run(h, run, false));
+    if (!phi || !mu_out) return fail(KG_EINVAL, "phi and mu_out must not be NULL");
+    KG_TRY(check_device(h));
+    const int R = run->n_vectors, M = run->n_moments;
+    KG_TRY(ensure_vectors(h, R, 3));
+    KG_TRY(ensure_moments(h, (size_t)R * M));
+    KG_TRY(copy_in(h, phi, V(h, 0), R));
+    KG_TRY(kpm_moments(h, R, M, true, V(h, 0), V(h, 0), V(h, 1), V(h, 2), (double2*)h->moments.p, M));
+    return copy_out(h, h->moments.p, mu_out, (size_t)R * M * sizeof(double2));
+}
+
+kg_status kg_vac(kg_hamiltonian* h, const kg_run* run, const double* phi, double* mu_out) {
+    clear_error();
+    KG_TRY(check_run(h, run, true));
+    if (!phi || !mu_out) return fail(KG_EINVAL, "phi and mu_out must not be NULL");
+    KG_TRY(check_device(h));
+    const int R = run->n_vectors, M = run->n_moments, NC = run->n_times;
+    Series ser;
+    if (NC > 1) KG_TRY(series_for(h, run->dt, run->bessel_tol, &ser));
+    // vectors: 0 A, 1 B, 2 A', 3 B', 4 L, 5 p1(A), 6 p1(B), 7 kpm b0, 8 kpm b1
+    KG_TRY(ensure_vectors(h, R, 9));
+    KG_TRY(ensure_moments(h, (size_t)R * NC * M));
+    double2 *A = V(h, 0), *B = V(h, 1), *A2 = V(h, 2), *B2 = V(h, 3), *L = V(h, 4);
+    const int grid = stream_grid(h->n * R);
+    const double vscale = h->emax / kHbarEvFs;
+    KG_TRY(copy_in(h, phi, A, R));
+    KG_CUDA_TRY(launch_apply(h->dev, R, 2, vscale, A, B, grid, h->stream));   // B = V phi
+    h->counters.other_launches += 1;
+    double2* mu = (double2*)h->moments.p;
+    for (int t = 0; t < NC; t++) {
+        if (t > 0) {
+            // A <- U(-dt) A, B <- U(-dt) B  (Eqs. 42-43)
+            double2* in[2] = {A, B};
+            double2* p1[2] = {V(h, 5), V(h, 6)};
+            double2* acc[2] = {A2, B2};
+            KG_TRY(run_series(h, R, ser, +1, 2, false, in, p1, acc, nullptr, nullptr, nullptr));
+            std::swap(A, A2);
+            std::swap(B, B2);
+        }
+        KG_CUDA_TRY(launch_apply(h->dev, R, 2, vscale, A, L, grid, h->stream));   // L = V A
+        h->counters.other_launches += 1;
+        KG_TRY(kpm_moments(h, R, M, false, L, B, V(h, 7), V(h, 8), mu + (int64_t)t * M,
+                           (int64_t)NC * M));
+    }
+    return copy_out(h, mu, mu_out, (size_t)R * NC * M * sizeof(double2));
+}
+
+kg_status kg_msd(kg_hamiltonian* h, const kg_run* run, const double* phi, double* mu_out) {
+    clear_error();
+    KG_TRY(check_run(h, run, true));
+    if (!phi || !mu_out) return fail(KG_EINVAL, "phi and mu_out must not be NULL");
+    KG_TRY(check_device(h));
+    const int R = run->n_vectors, M = run->n_moments, NC = run->n_times;
+    Series ser;
+    if (NC > 1) KG_TRY(series_for(h, run->dt, run->bessel_tol, &ser));
+    // vectors: 0 psi, 1 xi, 2 psi', 3 xi', 4 p1(xi), 5 p1(psi), 6 q1, 7 q0
+    KG_TRY(ensure_vectors(h, R, 8));
+    KG_TRY(ensure_moments(h, (size_t)R * NC * M));
+    double2 *psi = V(h, 0), *xi = V(h, 1), *psi2 = V(h, 2), *xi2 = V(h, 3);
+    KG_TRY(copy_in(h, phi, psi, R));
+    KG_CUDA_TRY(cudaMemsetAsync(xi, 0, vec_bytes(h, R), h->stream));   // [X, U(0)] = 0
+    double2* mu = (double2*)h->moments.p;
+    KG_CUDA_TRY(cudaMemsetAsync(mu, 0, (size_t)R * NC * M * sizeof(double2), h->stream));
+    for (int t = 1; t < NC; t++) {
+        // xi <- U(dt) xi + [X, U(dt)] psi ;  psi <- U(dt) psi  (Eq. 44)
+        double2* in[2] = {xi, psi};
+        double2* p1[2] = {V(h, 4), V(h, 5)};
+        double2* acc[2] = {xi2, psi2};
+        KG_TRY(run_series(h, R, ser, -1, 2, true, in, p1, acc, V(h, 6), V(h, 7), nullptr));
+        std::swap(xi, xi2);
+        std::swap(psi, psi2);
+        // moments of xi; scratch: the now-free chain buffers 4 and 5
+        KG_TRY(kpm_moments(h, R, M, true, xi, xi, V(h, 4), V(h, 5), mu + (int64_t)t * M,
+                           (int64_t)NC * M));
+    }
+    return copy_out(h, mu, mu_out, (size_t)R * NC * M * sizeof(double2));
+}
+
+kg_status kg_apply(kg_hamiltonian* h, int op, const double* in_dev, double* out_dev, int n_vectors) {
+    clear_error();
+    if (!h) return fail(KG_EINVAL, "hamiltonian is NULL");
+    if (op < KG_OP_H || op > KG_OP_V) return fail(KG_EINVAL, "unknown op");
+    if (!valid_r(n_vectors)) return fail(KG_EINVAL, "n_vectors must be a power of two in 1..64");
+    if (!in_dev || !out_dev || in_dev == out_dev) return fail(KG_EINVAL, "need distinct in/out");
+    KG_TRY(check_device(h));
+    const int R = n_vectors;
+    KG_TRY(ensure_vectors(h, R, 2));
+    KG_TRY(copy_in(h, in_dev, V(h, 0), R));
+    KG_CUDA_TRY(launch_apply(h->dev, R, op, h->emax / kHbarEvFs, V(h, 0), V(h, 1),
+                             stream_grid(h->n * R), h->stream));
+    h->counters.other_launches += 1;
+    return copy_out(h, V(h, 1), out_dev, (size_t)h->n * R * sizeof(double2));
+}
+
+kg_status kg_evolve(kg_hamiltonian* h, double dt, int which, double bessel_tol, const double* in_dev,
+                    double* out_dev, int n_vectors) {
+    clear_error();
+    if (!h) return fail(KG_EINVAL, "hamiltonian is NULL");
+    if (which < KG_U_FORWARD || which > KG_U_COMMUTATOR) return fail(KG_EINVAL, "unknown which");
+    if (!valid_r(n_vectors)) return fail(KG_EINVAL, "n_vectors must be a power of two in 1..64");
+    if (!in_dev || !out_dev || in_dev == out_dev) return fail(KG_EINVAL, "need distinct in/out");
+    KG_TRY(check_device(h));
+    const int R = n_vectors;
+    Series ser;
+    KG_TRY(series_for(h, dt, bessel_tol, &ser));
+    // vectors: 0 p0 (copy of in), 1 p1, 2 acc, 3 q1, 4 q0, 5 qacc
+    KG_TRY(ensure_vectors(h, R, 6));
+    KG_TRY(copy_in(h, in_dev, V(h, 0), R));
+    double2* in[1] = {V(h, 0)};
+    double2* p1[1] = {V(h, 1)};
+    double2* acc[1] = {V(h, 2)};
+    if (which == KG_U_COMMUTATOR) {
+        KG_TRY(run_series(h, R, ser, -1, 1, true, in, p1, acc, V(h, 3), V(h, 4), V(h, 5)));
+        return copy_out(h, V(h, 5), out_dev, (size_t)h->n * R * sizeof(double2));
+    }
+    KG_TRY(run_series(h, R, ser, which == KG_U_FORWARD ? -1 : +1, 1, false, in, p1, acc, nullptr,
+                      nullptr, nullptr));
+    return copy_out(h, V(h, 2), out_dev, (size_t)h->n * R * sizeof(double2));
+}
+
+kg_status kg_timing_enable(kg_hamiltonian* h, int enable) {
+    if (!h) return fail(KG_EINVAL, "hamiltonian is NULL");
+    cudaStreamSynchronize(h->stream);
+    for (auto& p : h->phases) {
+        h->spare_events.push_back(p.a);
+        h->spare_events.push_back(p.b);
+    }
+    h->phases.clear();
+    h->counters = kg_timing{};
+    h->timing = enable != 0;
+    return KG_OK;
+}
+
+kg_status kg_timing_read(kg_hamiltonian* h, kg_timing* out) {
+    if (!h || !out) return fail(KG_EINVAL, "NULL argument");
+    KG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    kg_timing t = h->counters;
+    t.kpm_ms = 0;
+    t.evolve_ms = 0;
+    for (auto& p : h->phases) {
+        float ms = 0;
+        KG_CUDA_TRY(cudaEventElapsedTime(&ms, p.a, p.b));
+        (p.kind == 0 ? t.kpm_ms : t.evolve_ms) += ms;
+    }
+    *out = t;
+    return KG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "kg.h"
+
+namespace kg {
+
+// hbar in eV fs (CODATA 2018) and h = 2 pi hbar.
+constexpr double kHbarEvFs = 0.6582119569;
+constexpr double kPi = 3.14159265358979323846;
+
+// Thread-local error message + status helpers.
+kg_status fail(kg_status code, const std::string& msg);
+void clear_error();
+
+#define KG_CUDA_TRY(expr)                                                              \
+    do {                                                                               \
+        cudaError_t kg_e_ = (expr);                                                    \
+        if (kg_e_ != cudaSuccess)                                                      \
+            return ::kg::fail(KG_ECUDA, std::string(#expr) + ": " +                    \
+                                            cudaGetErrorString(kg_e_));               \
+    } while (0)
+
+#define KG_TRY(expr)                    \
+    do {                                \
+        kg_status kg_s_ = (expr);       \
+        if (kg_s_ != KG_OK) return kg_s_; \
+    } while (0)
+
+// ---------------------------------------------------------------------------------
+// Host-side lattice (built once per Hamiltonian, then uploaded)
+// ---------------------------------------------------------------------------------
+
+struct HostLattice {
+    int kind = 0;
+    int64_t nx = 0, ny = 0, n = 0, n_active = 0;
+    std::vector<int32_t> idx;       // [3][n], -1 = no neighbour
+    std::vector<uint8_t> removed;   // [n]
+    std::vector<uint8_t> parity;    // [n] (i + j) & 1
+};
+
+// Validates the lattice description and fills the slot-major neighbour table.
+kg_status build_host_lattice(const kg_lattice* lat, const int64_t* vacancies, int64_t n_vac,
+                             HostLattice* out);
+
+// Displacement X_n - X_m (nm) of the bond in slot k of a site with parity p, along the
+// transport direction of the lattice kind.
+double slot_displacement(int kind, double bond_nm, int parity, int slot);
+
+// Bessel coefficients (host, FP64).
+kg_status bessel_series(double tau, double tol, int max_terms, double* j, int* n_terms);
+
+// ---------------------------------------------------------------------------------
+// Device-side description of H~ passed to every kernel launcher
+// ---------------------------------------------------------------------------------
+
+struct DevH {
+    const int32_t* idx = nullptr;   // [3][istride], sentinel = n (the zero row)
+    int64_t istride = 0;
+    int64_t n = 0;                  // sites; vectors have n + 1 rows (row n is zero)
+    const double* onsite = nullptr; // eps_n / E_max, or null
+    const uint8_t* parity = nullptr;// only for transport along y (AGNR)
+    double h = 0.0;                 // H~ hopping  -gamma0 / E_max
+    double dh[2][3] = {{0}};        // (X_n - X_m) * h per parity and slot (nm)
+    bool ytransport = false;
+};
+
+// Number of co-resident 256-thread CTAs per SM for a kernel, and the SM count.
+int sm_count();
+
+// ----- launchers (kg_kernels.cu); all return cudaError_t of the launch -----
+
+// KPM step with phi_L = phi_R (Chebyshev doubling): out = c H~ cur - prev (prev may be
+// null on the first step, then c = 1), partial[g][r][2] = (sum |cur|^2, sum Re conj(out) cur).
+cudaError_t launch_kpm_sym(const DevH& H, int R, bool first, const double2* cur,
+                           const double2* prev, double2* out, double* partial, int grid,
+                           cudaStream_t s);
+
+// KPM step with a separate phi_L: out = c H~ cur - prev; partial[g][r][2] = <L|out>.
+// On the first step partial[g][r][4] = (<L|out>, <L|cur>).
+cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const double2* L,
+                           const double2* cur, const double2* prev, double2* out,
+                           double* partial, int grid, cudaStream_t s);
+
+// Reduce per-block partials of a KPM run into moments mu[r * r_stride + n].
+//   first: partial [grid][R][A] of the first step (A = 2 sym, 4 gen)
+//   ring:  partial slabs [ring][grid][R][2]; slab (slab0 + b) % ring belongs to step n0 + b
+cudaError_t launch_reduce_first(const double* partial, int grid, int R, bool sym,
+                                double2* mu, int64_t r_stride, int M, cudaStream_t s);
+cudaError_t launch_reduce_ring(const double* ring, int slab0, int nslab, int ring_size,
+                               int grid, int R, bool sym, int n0, double2* mu,
+                               int64_t r_stride, int M, cudaStream_t s);
+
+struct Chains {
+    const double2* cur[3] = {nullptr, nullptr, nullptr};
+    const double2* prev[3] = {nullptr, nullptr, nullptr};
+    double2* nxt[3] = {nullptr, nullptr, nullptr};
+    double2* acc[3] = {nullptr, nullptr, nullptr};
+    // commutator chain [X, T_m(H~)] applied to chain nch-1
+    const double2* qcur = nullptr;
+    const double2* qprev = nullptr;
+    double2* qnxt = nullptr;
+    double2* qacc = nullptr;        // null: accumulate into acc[0]
+};
+
+// One term m of the Chebyshev-Bessel series on nch plain chains (+ the commutator
+// chain when xc).  first = the m = 1 step (also adds the J_0 term).
+cudaError_t launch_evolve(const DevH& H, int R, int nch, bool xc, bool first, double j0,
+                          double cr, double ci, const Chains& ch, int grid, cudaStream_t s);
+
+// out = op(in): 0 H~, 1 [X, H~], 2 V = -(i E_max / hbar)[X, H~] (scale = E_max / hbar).
+cudaError_t launch_apply(const DevH& H, int R, int op, double scale, const double2* in,
+                         double2* out, int grid, cudaStream_t s);
+
+// Grid size (CTAs) for a streaming kernel over n_items = n * R complex items.
+int stream_grid(int64_t n_items);
+
+}  // namespace kg

@@ -1,0 +1,440 @@
+// FP64 kernels of the Chebyshev recursion for sm_103a.
+//
+// Every kernel streams over the N*R complex items of a block of R vectors laid out
+// [N+1][R] (row N is a permanent zero row; the neighbour table points removed or
+// missing neighbours at it, so the gather needs no branch).  One thread owns items
+// w = n*R + r with a fixed r, so per-vector partial sums stay in registers; the
+// R vectors of a site share one load of the site's three neighbour indices.
+//
+// The GB300 executes FP64 at 1/64 of the FP32 rate (about 0.6e12 DFMA/s, and DADD
+// slower than DFMA), so the recursion is limited by the DP pipe, not by HBM.  The
+// kernels therefore express every FP64 operation as a fused multiply-add:
+// the neighbour sum and the "- T_{n-1}" are folded into the hopping multiply
+// (3 DFMA per real component), and each inner product costs 2 DFMA per component.
+#include <cuda_runtime.h>
+
+#include "kg_internal.h"
+
+namespace kg {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// --------------------------------------------------------------------------------
+// Block reduction of NACC per-thread accumulators belonging to vector r = tid % R.
+// Deterministic: fixed shuffle tree, then a fixed-order sum over warps.
+// dst receives [R][NACC] doubles for this block.
+// --------------------------------------------------------------------------------
+template <int R, int NACC>
+__device__ __forceinline__ void block_reduce(double (&acc)[NACC], double* __restrict__ dst) {
+    __shared__ double sm[kWarps][32][NACC];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (R < 32) {
+#pragma unroll
+        for (int off = 16; off >= R; off >>= 1) {
+#pragma unroll
+            for (int q = 0; q < NACC; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+        }
+    }
+    constexpr int kLanesUsed = R < 32 ? R : 32;
+    if (lane < kLanesUsed) {
+#pragma unroll
+        for (int q = 0; q < NACC; q++) sm[warp][lane][q] = acc[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < R) {
+        const int r = threadIdx.x;
+        constexpr int kGroups = R < 32 ? 1 : R / 32;
+        double s[NACC];
+#pragma unroll
+        for (int q = 0; q < NACC; q++) s[q] = 0.0;
+        for (int w = (R < 32 ? 0 : (r >> 5)); w < kWarps; w += kGroups) {
+#pragma unroll
+            for (int q = 0; q < NACC; q++) s[q] += sm[w][r & 31][q];
+        }
+#pragma unroll
+        for (int q = 0; q < NACC; q++) dst[r * NACC + q] = s[q];
+    }
+}
+
+struct Nbr {
+    double2 a, b, c, x;   // the three neighbours and the site itself
+};
+
+template <int R>
+__device__ __forceinline__ Nbr gather(const int32_t* __restrict__ idx, int64_t istride, int64_t n,
+                                      int r, const double2* __restrict__ v) {
+    const int32_t i0 = __ldg(idx + n), i1 = __ldg(idx + istride + n), i2 = __ldg(idx + 2 * istride + n);
+    Nbr g;
+    g.a = __ldg(v + (int64_t)i0 * R + r);
+    g.b = __ldg(v + (int64_t)i1 * R + r);
+    g.c = __ldg(v + (int64_t)i2 * R + r);
+    g.x = __ldg(v + n * R + r);
+    return g;
+}
+
+// y = c * (a + b + c3) + e * x - z   as a chain of fused multiply-adds (z may be 0).
+__device__ __forceinline__ double hop(double c, double a, double b, double c3, double e, double x,
+                                      double z, bool onsite) {
+    double t = onsite ? fma(e, x, -z) : -z;
+    return fma(c, a, fma(c, b, fma(c, c3, t)));
+}
+
+// --------------------------------------------------------------------------------
+// KPM step with phi_L = phi_R (DOS and MSD moments).  Uses the Chebyshev product
+// identity 2 T_m T_n = T_{m+n} + T_{|m-n|}, so one recursion step n yields two moments:
+//   mu_{2n} = 2 <phi_n|phi_n> - mu_0,   mu_{2n+1} = 2 <phi_{n+1}|phi_n> - mu_1
+// (both real for Hermitian H~).  The kernel computes phi_{n+1} = 2H~phi_n - phi_{n-1}
+// (first step: phi_1 = H~ phi_0) and the two per-block partial sums.
+// --------------------------------------------------------------------------------
+template <int R, bool ONSITE, bool FIRST>
+__global__ void __launch_bounds__(kThreads) kpm_sym_kernel(DevH H, const double2* __restrict__ cur,
+                                                           const double2* prev, double2* out,
+                                                           double* __restrict__ partial) {
+    const int64_t n_items = H.n * R;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int r = threadIdx.x & (R - 1);
+    const double c = FIRST ? H.h : 2.0 * H.h;
+    double acc[2] = {0.0, 0.0};
+    for (int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x; w < n_items; w += stride) {
+        const int64_t n = w / R;
+        const Nbr g = gather<R>(H.idx, H.istride, n, r, cur);
+        double e = 0.0;
+        if constexpr (ONSITE) e = (FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n);
+        double2 z = make_double2(0.0, 0.0);
+        if constexpr (!FIRST) z = prev[w];
+        const double yr = hop(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
+        const double yi = hop(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
+        out[w] = make_double2(yr, yi);
+        acc[0] = fma(g.x.x, g.x.x, fma(g.x.y, g.x.y, acc[0]));
+        acc[1] = fma(yr, g.x.x, fma(yi, g.x.y, acc[1]));
+    }
+    block_reduce<R, 2>(acc, partial + (int64_t)blockIdx.x * R * 2);
+}
+
+// --------------------------------------------------------------------------------
+// KPM step with a separate phi_L (VAC moments, Algorithm 5):
+//   phi_{n+1} = 2H~phi_n - phi_{n-1};  C_{n+1} = <phi_L|phi_{n+1}>
+// First step: phi_1 = H~ phi_0 and partials (<L|phi_1>, <L|phi_0>).
+// --------------------------------------------------------------------------------
+template <int R, bool ONSITE, bool FIRST>
+__global__ void __launch_bounds__(kThreads) kpm_gen_kernel(DevH H, const double2* __restrict__ L,
+                                                           const double2* __restrict__ cur,
+                                                           const double2* prev, double2* out,
+                                                           double* __restrict__ partial) {
+    constexpr int NACC = FIRST ? 4 : 2;
+    const int64_t n_items = H.n * R;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int r = threadIdx.x & (R - 1);
+    const double c = FIRST ? H.h : 2.0 * H.h;
+    double acc[NACC];
+#pragma unroll
+    for (int q = 0; q < NACC; q++) acc[q] = 0.0;
+    for (int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x; w < n_items; w += stride) {
+        const int64_t n = w / R;
+        const Nbr g = gather<R>(H.idx, H.istride, n, r, cur);
+        double e = 0.0;
+        if constexpr (ONSITE) e = (FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n);
+        double2 z = make_double2(0.0, 0.0);
+        if constexpr (!FIRST) z = prev[w];
+        const double yr = hop(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
+        const double yi = hop(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
+        out[w] = make_double2(yr, yi);
+        const double2 l = __ldg(L + w);
+        acc[0] = fma(l.x, yr, fma(l.y, yi, acc[0]));
+        acc[1] = fma(l.x, yi, fma(-l.y, yr, acc[1]));
+        if constexpr (FIRST) {
+            acc[2] = fma(l.x, g.x.x, fma(l.y, g.x.y, acc[2]));
+            acc[3] = fma(l.x, g.x.y, fma(-l.y, g.x.x, acc[3]));
+        }
+    }
+    block_reduce<R, NACC>(acc, partial + (int64_t)blockIdx.x * R * NACC);
+}
+
+// --------------------------------------------------------------------------------
+// Reductions of per-block partials into moments (fixed order => deterministic).
+// --------------------------------------------------------------------------------
+
+// Sum over g of part[g][R][A] for (r, q) -> out[r][q].  256 threads; pairs are
+// assigned round-robin, each pair's threads sum a strided subset then combine in a
+// fixed order through shared memory.
+__device__ void reduce_blocks(const double* __restrict__ part, int grid, int R, int A,
+                              double* __restrict__ out_rq) {
+    __shared__ double sm[kThreads];
+    const int pairs = R * A;
+    const int tpp = kThreads / pairs;   // threads per pair (>= 1, pairs <= 256)
+    const int t = threadIdx.x;
+    const int pair = t / tpp, sub = t % tpp;
+    double s = 0.0;
+    if (pair < pairs) {
+        const int r = pair / A, q = pair % A;
+        for (int g = sub; g < grid; g += tpp) s += part[((int64_t)g * R + r) * A + q];
+    }
+    sm[t] = s;
+    __syncthreads();
+    if (t < pairs) {
+        double v = 0.0;
+        for (int k = 0; k < tpp; k++) v += sm[t * tpp + k];
+        out_rq[t] = v;
+    }
+    __syncthreads();
+}
+
+__global__ void reduce_first_kernel(const double* __restrict__ part, int grid, int R, int sym,
+                                    double2* mu, int64_t r_stride, int M) {
+    __shared__ double res[kThreads];
+    const int A = sym ? 2 : 4;
+    reduce_blocks(part, grid, R, A, res);
+    if (threadIdx.x < R) {
+        const int r = threadIdx.x;
+        double2* m = mu + r * r_stride;
+        if (sym) {
+            m[0] = make_double2(res[r * 2 + 0], 0.0);
+            if (M > 1) m[1] = make_double2(res[r * 2 + 1], 0.0);
+        } else {
+            m[0] = make_double2(res[r * 4 + 2], res[r * 4 + 3]);
+            if (M > 1) m[1] = make_double2(res[r * 4 + 0], res[r * 4 + 1]);
+        }
+    }
+}
+
+__global__ void reduce_ring_kernel(const double* __restrict__ ring, int slab0, int ring_size,
+                                   int grid, int R, int sym, int n0, double2* mu, int64_t r_stride,
+                                   int M) {
+    __shared__ double res[kThreads];
+    const int slab = (slab0 + blockIdx.x) % ring_size;
+    const int n = n0 + blockIdx.x;   // recursion step that produced this slab
+    reduce_blocks(ring + (int64_t)slab * grid * R * 2, grid, R, 2, res);
+    if (threadIdx.x < R) {
+        const int r = threadIdx.x;
+        double2* m = mu + r * r_stride;
+        if (sym) {
+            const double mu0 = m[0].x, mu1 = m[1].x;
+            if (2 * n < M) m[2 * n] = make_double2(2.0 * res[r * 2] - mu0, 0.0);
+            if (2 * n + 1 < M) m[2 * n + 1] = make_double2(2.0 * res[r * 2 + 1] - mu1, 0.0);
+        } else {
+            if (n + 1 < M) m[n + 1] = make_double2(res[r * 2], res[r * 2 + 1]);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------------
+// One term of the Chebyshev-Bessel series (Algorithms 6 and 7) on NCH chains.
+// Plain chain k:   p_m = 2H~p_{m-1} - p_{m-2}  (first: p_1 = H~p_0)
+//                  acc_k += (cr + i ci) p_m    (first: acc_k = J_0 p_0 + (cr + i ci) p_1)
+// Commutator chain of the last plain chain s (Eq. 39):
+//                  q_m = 2[X,H~]p_{m-1} + 2H~q_{m-1} - q_{m-2}  (first: q_1 = [X,H~]p_0)
+//                  qacc += (cr + i ci) q_m  (into acc_0 when qacc is null)
+// [X,H~] has the same sparsity as H~ with per-slot factors (X_n - X_m) H~_nm, so it
+// reuses the gathered neighbours of chain s.
+// --------------------------------------------------------------------------------
+template <int R, int NCH, bool XC, bool FIRST, bool ONSITE, bool YPAR>
+__global__ void __launch_bounds__(kThreads) evolve_kernel(DevH H, double j0, double cr, double ci,
+                                                          Chains ch) {
+    const int64_t n_items = H.n * R;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int r = threadIdx.x & (R - 1);
+    const double c = FIRST ? H.h : 2.0 * H.h;
+    const double cx = FIRST ? 1.0 : 2.0;
+    const bool q_into_0 = (ch.qacc == nullptr);
+    for (int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x; w < n_items; w += stride) {
+        const int64_t n = w / R;
+        double e = 0.0;
+        if constexpr (ONSITE) e = (FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n);
+        double2 q_add = make_double2(0.0, 0.0);   // commutator contribution routed to acc_0
+        Nbr gs;
+#pragma unroll
+        for (int k = 0; k < NCH; k++) {
+            const Nbr g = gather<R>(H.idx, H.istride, n, r, ch.cur[k]);
+            if (k == NCH - 1) gs = g;
+            double2 z = make_double2(0.0, 0.0);
+            if constexpr (!FIRST) z = ch.prev[k][w];
+            const double yr = hop(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
+            const double yi = hop(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
+            ch.nxt[k][w] = make_double2(yr, yi);
+            double2 a;
+            if constexpr (FIRST) {
+                a = make_double2(j0 * g.x.x, j0 * g.x.y);
+            } else {
+                a = ch.acc[k][w];
+            }
+            a.x = fma(cr, yr, fma(-ci, yi, a.x));
+            a.y = fma(cr, yi, fma(ci, yr, a.y));
+            if (k == 0) {
+                q_add = a;   // finish acc_0 after the commutator chain
+            } else {
+                ch.acc[k][w] = a;
+            }
+        }
+        if constexpr (XC) {
+            // [X,H~] p_{m-1}: sum over slots of (X_n - X_m) H~_nm p[nbr]
+            double d0, d1, d2;
+            if constexpr (YPAR) {
+                const int p = __ldg(H.parity + n);
+                d0 = H.dh[p][0]; d1 = H.dh[p][1]; d2 = H.dh[p][2];
+            } else {
+                d0 = H.dh[0][0]; d1 = H.dh[0][1]; d2 = H.dh[0][2];
+            }
+            d0 *= cx; d1 *= cx; d2 *= cx;
+            double qr, qi;
+            if constexpr (FIRST) {
+                qr = fma(d0, gs.a.x, fma(d1, gs.b.x, d2 * gs.c.x));
+                qi = fma(d0, gs.a.y, fma(d1, gs.b.y, d2 * gs.c.y));
+            } else {
+                const Nbr gq = gather<R>(H.idx, H.istride, n, r, ch.qcur);
+                double2 qz = make_double2(0.0, 0.0);
+                if (ch.qprev) qz = ch.qprev[w];
+                qr = hop(c, gq.a.x, gq.b.x, gq.c.x, e, gq.x.x, qz.x, ONSITE);
+                qi = hop(c, gq.a.y, gq.b.y, gq.c.y, e, gq.x.y, qz.y, ONSITE);
+                qr = fma(d0, gs.a.x, fma(d1, gs.b.x, fma(d2, gs.c.x, qr)));
+                qi = fma(d0, gs.a.y, fma(d1, gs.b.y, fma(d2, gs.c.y, qi)));
+            }
+            ch.qnxt[w] = make_double2(qr, qi);
+            if (q_into_0) {
+                q_add.x = fma(cr, qr, fma(-ci, qi, q_add.x));
+                q_add.y = fma(cr, qi, fma(ci, qr, q_add.y));
+            } else {
+                double2 a = FIRST ? make_double2(0.0, 0.0) : ch.qacc[w];
+                a.x = fma(cr, qr, fma(-ci, qi, a.x));
+                a.y = fma(cr, qi, fma(ci, qr, a.y));
+                ch.qacc[w] = a;
+            }
+        }
+        ch.acc[0][w] = q_add;
+    }
+}
+
+// --------------------------------------------------------------------------------
+// out = H~ in, [X,H~] in, or V in = -(i E_max/hbar) [X,H~] in (Eq. 15).
+// --------------------------------------------------------------------------------
+template <int R, int OP, bool ONSITE, bool YPAR>
+__global__ void __launch_bounds__(kThreads) apply_kernel(DevH H, double scale,
+                                                         const double2* __restrict__ in,
+                                                         double2* __restrict__ out) {
+    const int64_t n_items = H.n * R;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int r = threadIdx.x & (R - 1);
+    for (int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x; w < n_items; w += stride) {
+        const int64_t n = w / R;
+        const Nbr g = gather<R>(H.idx, H.istride, n, r, in);
+        if constexpr (OP == 0) {
+            double e = 0.0;
+            if constexpr (ONSITE) e = __ldg(H.onsite + n);
+            out[w] = make_double2(hop(H.h, g.a.x, g.b.x, g.c.x, e, g.x.x, 0.0, ONSITE),
+                                  hop(H.h, g.a.y, g.b.y, g.c.y, e, g.x.y, 0.0, ONSITE));
+        } else {
+            double d0, d1, d2;
+            if constexpr (YPAR) {
+                const int p = __ldg(H.parity + n);
+                d0 = H.dh[p][0]; d1 = H.dh[p][1]; d2 = H.dh[p][2];
+            } else {
+                d0 = H.dh[0][0]; d1 = H.dh[0][1]; d2 = H.dh[0][2];
+            }
+            const double qr = fma(d0, g.a.x, fma(d1, g.b.x, d2 * g.c.x));
+            const double qi = fma(d0, g.a.y, fma(d1, g.b.y, d2 * g.c.y));
+            if constexpr (OP == 1) out[w] = make_double2(qr, qi);
+            else out[w] = make_double2(scale * qi, -scale * qr);   // -(i s)(qr + i qi)
+        }
+    }
+}
+
+// --------------------------------------------------------------------------------
+// Launchers: runtime (R, flags) -> template instantiation.
+// --------------------------------------------------------------------------------
+
+int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 1;
+    }
+    return sms;
+}
+
+int stream_grid(int64_t n_items) {
+    const int64_t need = (n_items + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)sm_count() * 6;   // a few resident waves worth of CTAs
+    int64_t g = need < cap ? need : cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+#define KG_DISPATCH_R(R_, ...)                                   \
+    switch (R_) {                                                \
+        case 1: { constexpr int RR = 1; __VA_ARGS__; } break;    \
+        case 2: { constexpr int RR = 2; __VA_ARGS__; } break;    \
+        case 4: { constexpr int RR = 4; __VA_ARGS__; } break;    \
+        case 8: { constexpr int RR = 8; __VA_ARGS__; } break;    \
+        case 16: { constexpr int RR = 16; __VA_ARGS__; } break;  \
+        case 32: { constexpr int RR = 32; __VA_ARGS__; } break;  \
+        case 64: { constexpr int RR = 64; __VA_ARGS__; } break;  \
+        default: return cudaErrorInvalidValue;                   \
+    }
+
+#define KG_BOOL(b_, NAME, ...)                         \
+    if (b_) { constexpr bool NAME = true; __VA_ARGS__; } \
+    else { constexpr bool NAME = false; __VA_ARGS__; }
+
+cudaError_t launch_kpm_sym(const DevH& H, int R, bool first, const double2* cur, const double2* prev,
+                           double2* out, double* partial, int grid, cudaStream_t s) {
+    const bool ons = H.onsite != nullptr;
+    KG_DISPATCH_R(R, KG_BOOL(ons, ON, KG_BOOL(first, FI,
+        kpm_sym_kernel<RR, ON, FI><<<grid, kThreads, 0, s>>>(H, cur, prev, out, partial))));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const double2* L, const double2* cur,
+                           const double2* prev, double2* out, double* partial, int grid,
+                           cudaStream_t s) {
+    const bool ons = H.onsite != nullptr;
+    KG_DISPATCH_R(R, KG_BOOL(ons, ON, KG_BOOL(first, FI,
+        kpm_gen_kernel<RR, ON, FI><<<grid, kThreads, 0, s>>>(H, L, cur, prev, out, partial))));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_first(const double* partial, int grid, int R, bool sym, double2* mu,
+                                int64_t r_stride, int M, cudaStream_t s) {
+    reduce_first_kernel<<<1, kThreads, 0, s>>>(partial, grid, R, sym ? 1 : 0, mu, r_stride, M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_ring(const double* ring, int slab0, int nslab, int ring_size, int grid,
+                               int R, bool sym, int n0, double2* mu, int64_t r_stride, int M,
+                               cudaStream_t s) {
+    if (nslab <= 0) return cudaSuccess;
+    reduce_ring_kernel<<<nslab, kThreads, 0, s>>>(ring, slab0, ring_size, grid, R, sym ? 1 : 0,
+                                                  n0, mu, r_stride, M);
+    return cudaGetLastError();
+}
+
+template <int R, int NCH, bool XC>
+static void evolve_dispatch(const DevH& H, bool first, double j0, double cr, double ci,
+                            const Chains& ch, int grid, cudaStream_t s) {
+    const bool ons = H.onsite != nullptr, ypar = H.ytransport;
+    KG_BOOL(first, FI, KG_BOOL(ons, ON, KG_BOOL(ypar, YP,
+        evolve_kernel<R, NCH, XC, FI, ON, YP><<<grid, kThreads, 0, s>>>(H, j0, cr, ci, ch))));
+}
+
+cudaError_t launch_evolve(const DevH& H, int R, int nch, bool xc, bool first, double j0, double cr,
+                          double ci, const Chains& ch, int grid, cudaStream_t s) {
+    if (nch < 1 || nch > 2) return cudaErrorInvalidValue;
+    KG_DISPATCH_R(R,
+        if (nch == 1 && !xc) evolve_dispatch<RR, 1, false>(H, first, j0, cr, ci, ch, grid, s);
+        else if (nch == 1) evolve_dispatch<RR, 1, true>(H, first, j0, cr, ci, ch, grid, s);
+        else if (!xc) evolve_dispatch<RR, 2, false>(H, first, j0, cr, ci, ch, grid, s);
+        else evolve_dispatch<RR, 2, true>(H, first, j0, cr, ci, ch, grid, s));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const DevH& H, int R, int op, double scale, const double2* in,
+                         double2* out, int grid, cudaStream_t s) {
+    const bool ons = H.onsite != nullptr, ypar = H.ytransport;
+    KG_DISPATCH_R(R, KG_BOOL(ons, ON, KG_BOOL(ypar, YP,
+        if (op == 0) apply_kernel<RR, 0, ON, YP><<<grid, kThreads, 0, s>>>(H, scale, in, out);
+        else if (op == 1) apply_kernel<RR, 1, ON, YP><<<grid, kThreads, 0, s>>>(H, scale, in, out);
+        else apply_kernel<RR, 2, ON, YP><<<grid, kThreads, 0, s>>>(H, scale, in, out))));
+    return cudaGetLastError();
+}
+
+}  // namespace kg

@@ -1,0 +1,105 @@
+"""CPU tests of the C-ABI library: it loads, exports every entry point that
+include/kg.h declares, and its host-side logic (neighbour table, Bessel
+coefficients, Jackson damping, Chebyshev sums, running conductivities) agrees
+with the oracle.  No GPU compute is called here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import kg_inputs as ki
+import oracle
+import paper_1307_0288_gb300 as kg
+from oracle import post
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(kg_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = kg.lib()
+    declared = _declared_functions()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert {n for n, _, _ in kg.ABI} == declared
+    assert kg.abi_version() == 1
+
+
+def test_neighbor_table_matches_oracle_lattice():
+    """The library's slot table (i-1, i+1, adjacent chain) and the oracle's
+    distance-based bond search give the same bonds (Sec. 2 lattice)."""
+    cases = [ki.sheet_cells(5, 4, vacancy_conc=0.05, lattice_seed=1),
+             ki.zgnr(7, 9, vacancy_conc=0.03, lattice_seed=2),
+             ki.Workload(ki.AGNR, 9, 12, vacancy_conc=0.04, lattice_seed=3),
+             ki.Workload(ki.SHEET, 4, 2),
+             ki.Workload(ki.AGNR, 2, 4)]
+    for w in cases:
+        idx = kg.lattice_neighbors(w.kind, w.nx, w.ny, w.vacancies)
+        h = oracle.from_workload(w)
+        for n in range(w.n_sites):
+            lib_set = sorted(int(m) for m in idx[:, n] if m >= 0)
+            ora_set = sorted(int(m) for m in h.col[h.row_ptr[n]:h.row_ptr[n + 1]])
+            assert lib_set == ora_set, (w.kind, n, lib_set, ora_set)
+
+
+def test_invalid_lattices_are_rejected():
+    for kind, nx, ny in [(ki.SHEET, 3, 4), (ki.SHEET, 2, 4), (ki.SHEET, 4, 3), (ki.ZGNR, 5, 3),
+                         (ki.AGNR, 1, 4), (ki.SHEET, 0, 4)]:
+        with pytest.raises(kg.KgError) as e:
+            kg.lattice_neighbors(kind, nx, ny)
+        assert e.value.status == -1
+    with pytest.raises(kg.KgError):
+        kg.lattice_neighbors(ki.SHEET, 8, 4, vacancies=[3, 3])
+    with pytest.raises(kg.KgError):
+        kg.lattice_neighbors(ki.SHEET, 8, 4, vacancies=[32])
+
+
+def test_bessel_series_matches_oracle():
+    """Eqs. 36-37: the library's J_m (trapezoid / power series) and N_p agree with the
+    oracle's Miller recurrence."""
+    for tau in [0.05, 0.41 * 3.15, np.pi, 3.15, 6.3, 9.45, 25.0]:
+        j = kg.bessel_series(tau, 1e-15)
+        jo, npo = oracle.bessel_series(tau, 1e-15)
+        assert len(j) == npo
+        assert np.max(np.abs(j - jo)) < 2e-16 * 8
+
+
+def test_jackson_and_kpm_sum_match_oracle():
+    m = 300
+    assert np.max(np.abs(kg.jackson(m) - oracle.jackson(m))) < 1e-15
+    rng = np.random.default_rng(0)
+    mu = rng.normal(size=(3, m)) * np.exp(-np.arange(m) / 60.0)
+    en = post.energy_grid()
+    ref = post.kpm_density(mu, en, 8.505, 123.4)
+    got = kg.kpm_sum(mu, en, 8.505, 123.4)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_conductivity_formulas_match_oracle():
+    rng = np.random.default_rng(1)
+    d = rng.normal(size=(12, 7))
+    t = post.time_grid(12, 2.0)
+    dt_fs = t[1]
+    assert np.allclose(kg.conductivity(kg.KG_SIGMA_GK, d, dt_fs), post.sigma_gk(d, t), rtol=1e-13, atol=1e-13)
+    assert np.allclose(kg.conductivity(kg.KG_SIGMA_E1, d, dt_fs), post.sigma_e1(d, t), rtol=1e-13, atol=1e-13)
+    assert np.allclose(kg.conductivity(kg.KG_SIGMA_E2, d, dt_fs), post.sigma_e2(d, t), rtol=1e-13, atol=1e-13)
+
+
+def test_gpu_entry_points_fail_loudly_without_a_device():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(kg.KgError) as e:
+        kg.build_hamiltonian(ki.SHEET, 8, 8, emax_ev=8.505)
+    assert e.value.status == -6

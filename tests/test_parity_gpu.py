@@ -1,0 +1,221 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same
+seeded Hamiltonians and random-phase vectors.
+
+Tolerance: relative error 1e-10 in FP64 with the norm
+    max_{n,t} |C_gpu - C_oracle| / max_{n,t} |C_oracle|   per random vector
+(the odd DOS moments are O(sqrt N) while C_0 = N, so element-wise relative error is
+not meaningful).  Vectors from single products / time steps are compared the same
+way at 1e-12.
+"""
+import numpy as np
+import pytest
+
+import kg_inputs as ki
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1307_0288_gb300 as kg  # noqa: E402
+
+TOL_MOMENTS = 1e-10
+TOL_VECTOR = 1e-12
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _rel_per_vector(gpu, ora):
+    return max(_rel(gpu[r], ora[r]) for r in range(len(ora)))
+
+
+def _systems():
+    return [
+        ki.sheet_cells(8, 6, vacancy_conc=0.04, anderson_w_ev=1.0, lattice_seed=17),
+        ki.zgnr(9, 14, anderson_w_ev=1.5, vacancy_conc=0.01, lattice_seed=18),
+        ki.Workload(ki.AGNR, 9, 24, vacancy_conc=0.03, lattice_seed=19),
+        ki.sheet_cells(25, 13, vacancy_conc=0.01, lattice_seed=20),   # 1300 sites: ragged tail
+    ]
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+# ------------------------------------------------------------------ single operators
+
+@pytest.mark.parametrize("r", [1, 4])
+def test_apply_matches_oracle(r):
+    for w in _systems():
+        h = kg.from_workload(w)
+        ho = oracle.from_workload(w)
+        phi = w.vectors(r)
+        x = _dev(phi)
+        out = torch.empty_like(x)
+        for op, ref in [(kg.KG_OP_H, oracle.apply_h), (kg.KG_OP_XH, oracle.apply_xh),
+                        (kg.KG_OP_V, oracle.apply_v)]:
+            kg.apply(h, op, x, out)
+            got = out.cpu().numpy()
+            want = np.stack([ref(ho, phi[:, k]) for k in range(r)], axis=1)
+            assert _rel(got, want) < TOL_VECTOR, (w.kind, op)
+
+
+@pytest.mark.parametrize("dt", [0.41, 2.0])
+def test_evolve_matches_oracle(dt):
+    for w in _systems():
+        h = kg.from_workload(w)
+        ho = oracle.from_workload(w)
+        tau = oracle.tau_of(ho, dt)
+        phi = w.vectors(2)
+        x = _dev(phi)
+        out = torch.empty_like(x)
+        for which, ref in [(kg.KG_U_FORWARD, lambda v: oracle.evolve(ho, v, tau, +1)),
+                           (kg.KG_U_BACKWARD, lambda v: oracle.evolve(ho, v, tau, -1)),
+                           (kg.KG_U_COMMUTATOR, lambda v: oracle.evolvex(ho, v, tau))]:
+            kg.evolve(h, dt, which, x, out)
+            got = out.cpu().numpy()
+            want = np.stack([ref(phi[:, k]) for k in range(2)], axis=1)
+            assert _rel(got, want) < TOL_VECTOR, (w.kind, which)
+
+
+# ------------------------------------------------------------------ DOS moments
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 7, 64, 513])
+def test_dos_moments_match_oracle(m):
+    for w in _systems():
+        h = kg.from_workload(w)
+        ho = oracle.from_workload(w)
+        phi = w.vectors(4)
+        got = kg.dos_moments(h, phi, m)
+        want = np.stack([oracle.kpm_moments(ho, phi[:, r], phi[:, r], m) for r in range(4)])
+        assert _rel_per_vector(got, want) < TOL_MOMENTS, (w.kind, m)
+
+
+@pytest.mark.parametrize("r", [1, 2, 8, 16, 32, 64])
+def test_dos_moments_every_block_width(r):
+    w = ki.zgnr(8, 40, anderson_w_ev=0.8, lattice_seed=21)
+    h = kg.from_workload(w)
+    ho = oracle.from_workload(w)
+    phi = w.vectors(r)
+    got = kg.dos_moments(h, phi, 100)
+    want = np.stack([oracle.kpm_moments(ho, phi[:, k], phi[:, k], 100) for k in range(r)])
+    assert _rel_per_vector(got, want) < TOL_MOMENTS
+
+
+# ------------------------------------------------------------------ VAC / MSD
+
+def test_vac_matches_oracle_small_sheet_4096_sites():
+    """32 x 32 cells (4096 sites), 1 % vacancies, M = 512, one vector, 10 steps of
+    dt = 1 hbar/gamma0: the full small VAC workload."""
+    w = ki.sheet_cells(32, 32, vacancy_conc=0.01)
+    h = kg.from_workload(w)
+    ho = oracle.from_workload(w)
+    phi = w.vectors(1)
+    got = kg.vac(h, phi, 512, 10, 1.0)
+    want = oracle.vac_moments(ho, phi[:, 0], 512, 10, 1.0)
+    assert _rel(got[0], want) < TOL_MOMENTS
+
+
+@pytest.mark.parametrize("w", [ki.zgnr(10, 30, anderson_w_ev=2.0, vacancy_conc=0.01, lattice_seed=4),
+                               ki.Workload(ki.AGNR, 11, 40, vacancy_conc=0.02, lattice_seed=5)])
+def test_vac_matches_oracle_ribbons(w):
+    h = kg.from_workload(w)
+    ho = oracle.from_workload(w)
+    phi = w.vectors(2)
+    got = kg.vac(h, phi, 96, 4, 2.0)
+    for r in range(2):
+        want = oracle.vac_moments(ho, phi[:, r], 96, 4, 2.0)
+        assert _rel(got[r], want) < TOL_MOMENTS
+
+
+def test_msd_matches_oracle_medium_sheet():
+    """128 x 64 cells (32768 sites), 0.5 % vacancies, M = 400, 2 vectors, 4 steps of
+    dt = 2 hbar/gamma0 (tau = 6.3, N_p = 28)."""
+    w = ki.sheet_cells(128, 64, vacancy_conc=0.005)
+    h = kg.from_workload(w)
+    ho = oracle.from_workload(w)
+    phi = w.vectors(2)
+    got = kg.msd(h, phi, 400, 4, 2.0)
+    assert np.all(got[:, 0] == 0)
+    for r in range(2):
+        want = oracle.msd_moments(ho, phi[:, r], 400, 4, 2.0)
+        assert _rel(got[r], want) < TOL_MOMENTS
+
+
+@pytest.mark.parametrize("w", [ki.zgnr(10, 30, anderson_w_ev=2.0, vacancy_conc=0.01, lattice_seed=6),
+                               ki.Workload(ki.AGNR, 11, 40, vacancy_conc=0.02, lattice_seed=7)])
+def test_msd_matches_oracle_ribbons(w):
+    h = kg.from_workload(w)
+    ho = oracle.from_workload(w)
+    phi = w.vectors(4)
+    got = kg.msd(h, phi, 65, 3, 1.5)
+    for r in range(4):
+        want = oracle.msd_moments(ho, phi[:, r], 65, 3, 1.5)
+        assert _rel(got[r], want) < TOL_MOMENTS
+
+
+def test_full_size_msd_sheet_sampled():
+    """2048 x 1024 sites (2,097,152), 0.5 % vacancies, 4 vectors, M = 3000, dt = 2, in the
+    launch configuration of the benchmark.  The oracle evaluates one time step and the
+    first 24 moments of each vector; all 3000 moments obey |C_n| <= C_0 (Chebyshev bound
+    |T_n| <= 1 on the spectrum of H~)."""
+    w = ki.sheet_cells(1024, 512, vacancy_conc=0.005, n_vec=4)
+    h = kg.from_workload(w)
+    phi = w.vectors(4)
+    got = kg.msd(h, phi, 3000, 2, 2.0)
+    c = got[:, 1]
+    assert np.all(np.abs(c.imag) == 0)
+    assert np.all(np.abs(c.real) <= c[:, :1].real * (1 + 1e-12))
+    ho = oracle.from_workload(w)
+    for r in range(4):
+        want = oracle.msd_moments(ho, phi[:, r], 24, 2, 2.0)[1]
+        assert _rel(c[r, :24], want) < TOL_MOMENTS
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_all_sites_removed_gives_zero_moments():
+    w = ki.Workload(ki.SHEET, 8, 4, vacancy_conc=1.0)
+    h = kg.from_workload(w)
+    phi = np.ones((w.n_sites, 2), dtype=np.complex128)
+    assert np.all(kg.dos_moments(h, phi, 9) == 0)
+    assert np.all(kg.vac(h, phi, 9, 3, 1.0) == 0)
+
+
+def test_single_time_has_no_evolution():
+    w = _systems()[0]
+    h = kg.from_workload(w)
+    ho = oracle.from_workload(w)
+    phi = w.vectors(1)
+    got = kg.vac(h, phi, 33, 1, 1.0)
+    want = oracle.vac_moments(ho, phi[:, 0], 33, 1, 1.0)
+    assert _rel(got[0], want) < TOL_MOMENTS
+    assert np.all(kg.msd(h, phi, 33, 1, 1.0) == 0)
+
+
+def test_device_and_host_buffers_give_identical_results():
+    w = _systems()[1]
+    h = kg.from_workload(w)
+    phi = w.vectors(4)
+    host = kg.msd(h, phi, 50, 3, 1.0)
+    out = torch.zeros((4, 3, 50), dtype=torch.complex128, device="cuda")
+    kg.msd(h, _dev(phi), 50, 3, 1.0, out=out)
+    assert np.array_equal(out.cpu().numpy(), host)
+    again = kg.msd(h, phi, 50, 3, 1.0)
+    assert np.array_equal(again, host)           # deterministic reductions
+
+
+def test_invalid_runs_are_rejected():
+    w = _systems()[0]
+    h = kg.from_workload(w)
+    phi = w.vectors(3)
+    with pytest.raises(ValueError):
+        kg.dos_moments(h, np.zeros((5, 1)), 10)
+    with pytest.raises(kg.KgError):
+        kg.dos_moments(h, phi, 10)              # R = 3 is not a power of two
+    with pytest.raises(kg.KgError):
+        kg.vac(h, w.vectors(1), 10, 3, -1.0)
+    with pytest.raises(kg.KgError):
+        kg.dos_moments(h, w.vectors(1), 0)
