@@ -176,12 +176,19 @@ def test_full_size_msd_sheet_sampled():
 
 # ------------------------------------------------------------------ edge cases
 
-def test_all_sites_removed_gives_zero_moments():
+def test_all_sites_removed():
+    """Every atom removed: trace vectors are zero there, so all moments vanish.  A
+    caller's nonzero amplitude on removed atoms behaves as isolated E = 0 sites
+    (empty rows of H~), identically in the oracle."""
     w = ki.Workload(ki.SHEET, 8, 4, vacancy_conc=1.0)
     h = kg.from_workload(w)
-    phi = np.ones((w.n_sites, 2), dtype=np.complex128)
-    assert np.all(kg.dos_moments(h, phi, 9) == 0)
-    assert np.all(kg.vac(h, phi, 9, 3, 1.0) == 0)
+    assert np.all(kg.dos_moments(h, w.vectors(2), 9) == 0)
+    assert np.all(kg.vac(h, w.vectors(2), 9, 3, 1.0) == 0)
+    ones = np.ones((w.n_sites, 2), dtype=np.complex128)
+    ho = oracle.from_workload(w)
+    got = kg.dos_moments(h, ones, 9)
+    want = oracle.kpm_moments(ho, ones[:, 0], ones[:, 0], 9)
+    assert _rel(got[0], want) < TOL_MOMENTS
 
 
 def test_single_time_has_no_evolution():
