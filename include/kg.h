@@ -160,6 +160,33 @@ kg_status kg_apply(kg_hamiltonian* h, int op, const double* in_dev, double* out_
 kg_status kg_evolve(kg_hamiltonian* h, double dt, int which, double bessel_tol,
                     const double* in_dev, double* out_dev, int n_vectors);
 
+/* DOS moments without device memory allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (their device memory is owned by a host framework's allocator, or they
+ * must not allocate once they are serving).  It computes the same moments as
+ * kg_dos_moments (C_n = <phi|T_n(H~)|phi>, n < M, for R vectors) but builds no
+ * kg_hamiltonian and allocates nothing: its scratch space is one file-scope device
+ * array of KG_NOALLOC_SCRATCH_BYTES, reserved when the library's device code is
+ * loaded on a GPU and held there until the process exits.
+ *   idx_dev     device int32 [3][N], the neighbour table of kg_lattice_neighbors
+ *               (slot-major, -1 where absent).
+ *   onsite_dev  device double [N], scaled on-site energies eps_n / E_max, or NULL.
+ *   n_sites     N.   hopping: the scaled hopping -gamma0 / E_max (0 < |h| < 1/3).
+ *   n_vectors   R, a power of two in 1..64.   n_moments: M >= 1.
+ *   phi_dev     device [N][R][2] random vectors;  mu_dev: device [R][M][2] output.
+ *   cuda_stream stream the work is issued on; the call returns after it completes.
+ * Scratch needed: 12 N + 48 (N + 1) R bytes plus about 0.5 MB x R of partial sums;
+ * larger problems are rejected with KG_EINVAL and a message giving both sizes.
+ * The first call on a device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  Every call shares the
+ * one array and overwrites it, so calls that overlap on the GPU (several streams or
+ * host threads at once) race; serialise them. */
+#define KG_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+kg_status kg_dos_moments_noalloc(const int32_t* idx_dev, const double* onsite_dev, int64_t n_sites,
+                                 double hopping, int n_vectors, int n_moments,
+                                 const double* phi_dev, double* mu_dev, void* cuda_stream);
+
 /* ------------------------------------------------------------------------- */
 /* Timing counters (filled by the GPU entry points above)                    */
 /* ------------------------------------------------------------------------- */

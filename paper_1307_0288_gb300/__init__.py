@@ -76,6 +76,7 @@ ABI = [
     ("kg_jackson", _I, [_I, _P]),
     ("kg_kpm_sum", _I, [_P, _I, _I, _P, _I, _D, _D, _P]),
     ("kg_conductivity", _I, [_I, _P, _I, _I, _D, _P]),
+    ("kg_dos_moments_noalloc", _I, [_P, _P, _I64, _D, _I, _I, _P, _P, _P]),
 ]
 
 _lib = None
@@ -279,6 +280,23 @@ def evolve(h: Hamiltonian, dt: float, which: int, x, out, bessel_tol: float = 1e
     _check(lib().kg_evolve(h.handle, float(dt), int(which), float(bessel_tol),
                            ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), r))
     return out
+
+
+def dos_moments_noalloc(idx_dev, onsite_dev, n_sites: int, hopping: float, phi_dev, mu_dev,
+                        stream=None):
+    """kg_dos_moments_noalloc on caller-owned device tensors (no device allocation).
+
+    idx_dev int32 [3][N] (-1 = absent), onsite_dev float64 [N] (eps/E_max) or None,
+    phi_dev complex128 [N] or [N][R], mu_dev complex128 [R][M] (written)."""
+    r = _nvec(phi_dev, n_sites)
+    m = int(mu_dev.shape[-1])
+    s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(lib().kg_dos_moments_noalloc(
+        ctypes.c_void_p(idx_dev.data_ptr()),
+        None if onsite_dev is None else ctypes.c_void_p(onsite_dev.data_ptr()),
+        int(n_sites), float(hopping), r, m, ctypes.c_void_p(phi_dev.data_ptr()),
+        ctypes.c_void_p(mu_dev.data_ptr()), ctypes.c_void_p(s)))
+    return mu_dev
 
 
 def timing_enable(h: Hamiltonian, enable: bool = True):
