@@ -168,7 +168,7 @@ static kg_status kpm_moments(kg_hamiltonian* h, int R, int M, bool sym, const do
                              const double2* phi_r, double2* b0, double2* b1, double2* mu,
                              int64_t r_stride) {
     PhaseTimer t(h, 0);
-    const int grid = stream_grid(h->n * R);
+    const int grid = kpm_grid(h->dev, R, sym);
     KG_TRY(ensure_partials(h, R, grid));
     double* pf = (double*)h->part_first.p;
     double* ring = (double*)h->part_ring.p;

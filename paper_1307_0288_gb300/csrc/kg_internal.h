@@ -120,5 +120,7 @@ cudaError_t launch_apply(const DevH& H, int R, int op, double scale, const doubl
 
 // Grid size (CTAs) for a streaming kernel over n_items = n * R complex items.
 int stream_grid(int64_t n_items);
+// One full resident wave of the (non-first) KPM step kernel for this H and R.
+int kpm_grid(const DevH& H, int R, bool sym);
 
 }  // namespace kg

@@ -13,6 +13,8 @@
 // (3 DFMA per real component), and each inner product costs 2 DFMA per component.
 #include <cuda_runtime.h>
 
+#include <unordered_map>
+
 #include "kg_internal.h"
 
 namespace kg {
@@ -228,7 +230,20 @@ __global__ void reduce_ring_kernel(const double* __restrict__ ring, int slab0, i
 // [X,H~] has the same sparsity as H~ with per-slot factors (X_n - X_m) H~_nm, so it
 // reuses the gathered neighbours of chain s.
 // --------------------------------------------------------------------------------
-template <int R, int NCH, bool XC, bool FIRST, bool ONSITE, bool YPAR>
+// (s i)^m is real for even m and imaginary for odd m, so ODD selects the two FMAs that
+// the non-zero part of the coefficient needs: acc += cr * y  or  acc += i ci * y.
+__device__ __forceinline__ void add_term(double2& a, bool odd, double cr, double ci, double yr,
+                                         double yi) {
+    if (odd) {
+        a.x = fma(-ci, yi, a.x);
+        a.y = fma(ci, yr, a.y);
+    } else {
+        a.x = fma(cr, yr, a.x);
+        a.y = fma(cr, yi, a.y);
+    }
+}
+
+template <int R, int NCH, bool XC, bool FIRST, bool ONSITE, bool YPAR, bool ODD>
 __global__ void __launch_bounds__(kThreads) evolve_kernel(DevH H, double j0, double cr, double ci,
                                                           Chains ch) {
     const int64_t n_items = H.n * R;
@@ -258,8 +273,7 @@ __global__ void __launch_bounds__(kThreads) evolve_kernel(DevH H, double j0, dou
             } else {
                 a = ch.acc[k][w];
             }
-            a.x = fma(cr, yr, fma(-ci, yi, a.x));
-            a.y = fma(cr, yi, fma(ci, yr, a.y));
+            add_term(a, ODD, cr, ci, yr, yi);
             if (k == 0) {
                 q_add = a;   // finish acc_0 after the commutator chain
             } else {
@@ -291,12 +305,10 @@ __global__ void __launch_bounds__(kThreads) evolve_kernel(DevH H, double j0, dou
             }
             ch.qnxt[w] = make_double2(qr, qi);
             if (q_into_0) {
-                q_add.x = fma(cr, qr, fma(-ci, qi, q_add.x));
-                q_add.y = fma(cr, qi, fma(ci, qr, q_add.y));
+                add_term(q_add, ODD, cr, ci, qr, qi);
             } else {
                 double2 a = FIRST ? make_double2(0.0, 0.0) : ch.qacc[w];
-                a.x = fma(cr, qr, fma(-ci, qi, a.x));
-                a.y = fma(cr, qi, fma(ci, qr, a.y));
+                add_term(a, ODD, cr, ci, qr, qi);
                 ch.qacc[w] = a;
             }
         }
@@ -360,6 +372,30 @@ int stream_grid(int64_t n_items) {
     return (int)(g < 1 ? 1 : g);
 }
 
+// Exactly one resident wave of a grid-stride kernel: SMs x co-resident CTAs per SM,
+// capped by the work.  A partial second wave would leave most SMs idle at the end of
+// every launch (the DP pipe is the bottleneck, so the tail costs its full share).
+template <typename K>
+static int one_wave_grid(K kernel, int64_t n_items) {
+    static thread_local std::unordered_map<const void*, int> cache;
+    int per_sm = 0;
+    auto it = cache.find((const void*)kernel);
+    if (it != cache.end()) {
+        per_sm = it->second;
+    } else {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        cache[(const void*)kernel] = per_sm;
+    }
+    const int64_t need = (n_items + kThreads - 1) / kThreads;
+    const int64_t wave = (int64_t)sm_count() * per_sm;
+    const int64_t g = need < wave ? need : wave;
+    return (int)(g < 1 ? 1 : g);
+}
+
 #define KG_DISPATCH_R(R_, ...)                                   \
     switch (R_) {                                                \
         case 1: { constexpr int RR = 1; __VA_ARGS__; } break;    \
@@ -393,6 +429,25 @@ cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const double2* L, c
     return cudaGetLastError();
 }
 
+int kpm_grid(const DevH& H, int R, bool sym) {
+    const bool ons = H.onsite != nullptr;
+    const int64_t items = H.n * R;
+    int g = 1;
+    auto pick = [&](auto k) { g = one_wave_grid(k, items); };
+    switch (R) {
+#define KG_KPM_GRID_CASE(RV)                                                                  \
+        case RV:                                                                             \
+            if (sym) { if (ons) pick(kpm_sym_kernel<RV, true, false>); else pick(kpm_sym_kernel<RV, false, false>); } \
+            else { if (ons) pick(kpm_gen_kernel<RV, true, false>); else pick(kpm_gen_kernel<RV, false, false>); }     \
+            break;
+        KG_KPM_GRID_CASE(1) KG_KPM_GRID_CASE(2) KG_KPM_GRID_CASE(4) KG_KPM_GRID_CASE(8)
+        KG_KPM_GRID_CASE(16) KG_KPM_GRID_CASE(32) KG_KPM_GRID_CASE(64)
+#undef KG_KPM_GRID_CASE
+        default: g = stream_grid(items);
+    }
+    return g;
+}
+
 cudaError_t launch_reduce_first(const double* partial, int grid, int R, bool sym, double2* mu,
                                 int64_t r_stride, int M, cudaStream_t s) {
     reduce_first_kernel<<<1, kThreads, 0, s>>>(partial, grid, R, sym ? 1 : 0, mu, r_stride, M);
@@ -410,10 +465,14 @@ cudaError_t launch_reduce_ring(const double* ring, int slab0, int nslab, int rin
 
 template <int R, int NCH, bool XC>
 static void evolve_dispatch(const DevH& H, bool first, double j0, double cr, double ci,
-                            const Chains& ch, int grid, cudaStream_t s) {
+                            const Chains& ch, int /*grid*/, cudaStream_t s) {
     const bool ons = H.onsite != nullptr, ypar = H.ytransport;
-    KG_BOOL(first, FI, KG_BOOL(ons, ON, KG_BOOL(ypar, YP,
-        evolve_kernel<R, NCH, XC, FI, ON, YP><<<grid, kThreads, 0, s>>>(H, j0, cr, ci, ch))));
+    const bool odd = first || cr == 0.0;   // the first step is the m = 1 term
+    KG_BOOL(first, FI, KG_BOOL(ons, ON, KG_BOOL(ypar, YP, KG_BOOL(odd, OD,
+        if constexpr (!FI || OD) {
+            const int g = one_wave_grid(evolve_kernel<R, NCH, XC, FI, ON, YP, OD>, H.n * R);
+            evolve_kernel<R, NCH, XC, FI, ON, YP, OD><<<g, kThreads, 0, s>>>(H, j0, cr, ci, ch);
+        }))));
 }
 
 cudaError_t launch_evolve(const DevH& H, int R, int nch, bool xc, bool first, double j0, double cr,
