@@ -59,6 +59,26 @@ def paper_work_per_step(n_sites: int, n_vec: int, n_moments: int, n_p: int) -> f
     return float(n_sites) * n_vec * ((n_moments - 1) + 4 * (n_p - 1))
 
 
+def _profiled_traffic(kernel_file: str, profile: str):
+    """DRAM bytes per launch from a committed ncu summary, or None when the kernel
+    source changed since the counters were taken."""
+    import hashlib
+    try:
+        src = open(os.path.join(ROOT, "paper_1307_0288_gb300", "csrc", kernel_file), "rb").read()
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    fields = dict(line.split(":", 1) for line in text.splitlines()
+                  if line.startswith(("kernel_source_sha256_16:", "traffic_bytes_per_launch:")))
+    if fields.get("kernel_source_sha256_16", "").strip() != sha:
+        return None
+    try:
+        return int(fields["traffic_bytes_per_launch"].strip())
+    except (KeyError, ValueError):
+        return None
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -273,7 +293,9 @@ def run_ours(args):
                    "parallelism": f"replicas x{world} (independent random vectors)"},
         "roofline": {"bound": "alu", "kernel": "kpm_sym_kernel (FP64 doubling KPM step)",
                      "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                     "traffic": _profiled_traffic("kg_kernels.cu", "kpm_sym_kernel_msd_sheet_2M.md"),
+                     "algorithmic_bytes": bytes_per_launch,
                      "peak_source": "nominal FP64 of the profiling recipe (DFMA probe: 1.20)",
                      "avg_launch_ms": kpm_launch_ms,
                      "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak,
