@@ -35,17 +35,19 @@ sys.path.insert(0, ROOT)
 
 import kg_inputs as ki  # noqa: E402
 
-CELLS = (1024, 512)
-VAC = 0.005
-R = 4
-M = 3000
-DT = 2.0
 TOL = 1e-15
+# name -> (cells, vacancy concentration, vectors per GPU, moments, dt, precision)
+WORKLOADS = {
+    "msd-sheet-2048x1024-vac0.5pct-R4-M3000-dt2": ((1024, 512), 0.005, 4, 3000, 2.0, "f64"),
+    "msd-sheet-4096x2048-vac1pct-R8-M6000-dt2-c64": ((2048, 1024), 0.01, 8, 6000, 2.0, "c64"),
+}
+DEFAULT_WORKLOAD = "msd-sheet-2048x1024-vac0.5pct-R4-M3000-dt2"
+CELLS, VAC, R, M, DT, PREC = WORKLOADS[DEFAULT_WORKLOAD]
 METRIC = "Chebyshev site-updates/s and HBM GB/s vs peak; σ(E,t) time at 1e-5 err vs FP64"
 UNIT = "site-updates/s"
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (profiling recipe table); DFMA probe measured 1.20
 KPM_FLOPS_PER_SITE_STEP = 16   # algorithmic FP64 flops of one doubling-KPM site update
-CONFIG_NAME = "msd-sheet-2048x1024-vac0.5pct-R4-M3000-dt2"
+CONFIG_NAME = DEFAULT_WORKLOAD
 
 
 def _env_int(name, default):
@@ -224,10 +226,11 @@ def run_ours(args):
     phi_host = torch.from_numpy(w.vectors(R)).pin_memory()
     phi_dev = phi_host.to("cuda")
     K, W = args.steps, args.warmup
+    prec = kg.KG_C64 if PREC == "c64" else kg.KG_FP64
 
     # warm-up: W correlation times
     out_w = torch.zeros((R, W + 1, M), dtype=torch.complex128, device="cuda")
-    kg.msd(h, phi_dev, M, W + 1, DT, bessel_tol=TOL, out=out_w)
+    kg.msd(h, phi_dev, M, W + 1, DT, bessel_tol=TOL, out=out_w, precision=prec)
     torch.cuda.synchronize()
 
     # timed region (device-resident inputs and outputs)
@@ -241,7 +244,7 @@ def run_ours(args):
     if clocks:
         clocks.start()
     e0.record(stream)
-    kg.msd(h, phi_dev, M, K + 1, DT, bessel_tol=TOL, out=out)
+    kg.msd(h, phi_dev, M, K + 1, DT, bessel_tol=TOL, out=out, precision=prec)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -259,7 +262,7 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    kg.msd(h, phi_host, M, K + 1, DT, bessel_tol=TOL, out=out_host)
+    kg.msd(h, phi_host, M, K + 1, DT, bessel_tol=TOL, out=out_host, precision=prec)
     e2e_s = time.perf_counter() - t0
     barrier()
     if dist is not None:
@@ -277,30 +280,40 @@ def run_ours(args):
     kpm_launch_ms = cnt["kpm_ms"] / max(cnt["kpm_launches"], 1)
     flops_per_launch = KPM_FLOPS_PER_SITE_STEP * w.n_sites * R
     achieved_tflops = flops_per_launch / (kpm_launch_ms * 1e-3) / 1e12
-    bytes_per_launch = w.n_sites * (12 + 48 * R)
+    vec_b = 16 if PREC == "f64" else 8
+    bytes_per_launch = w.n_sites * (12 + 3 * vec_b * R)
     achieved_gbs = bytes_per_launch / (kpm_launch_ms * 1e-3) / 1e9
     peaks = _peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback"
+    if PREC == "f64":
+        roofline = {"bound": "alu", "kernel": "kpm_sym_kernel<double> (FP64 doubling KPM step)",
+                    "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                    "traffic": _profiled_traffic("kg_kernels.cu", "kpm_sym_kernel_msd_sheet_2M.md"),
+                    "algorithmic_bytes": bytes_per_launch,
+                    "peak_source": "nominal FP64 of the profiling recipe (DFMA probe: 1.20)",
+                    "avg_launch_ms": kpm_launch_ms,
+                    "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak,
+                            "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}}
+    else:
+        roofline = {"bound": "hbm", "kernel": "kpm_sym_kernel<float> (complex64 doubling KPM step)",
+                    "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm_peak,
+                    "traffic": _profiled_traffic("kg_kernels.cu", "kpm_sym_kernel_c64_sheet_8M.md"),
+                    "algorithmic_bytes": bytes_per_launch, "peak_source": hbm_src,
+                    "avg_launch_ms": kpm_launch_ms}
     if rank != 0:
         return
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": PREC, "data": "synthetic",
         "config": {"workload": CONFIG_NAME, "sites": w.n_sites, "vacancies": len(w.vacancies),
                    "vectors_per_gpu": R, "moments": M, "dt_hbar_over_gamma0": DT, "bessel_terms": n_p,
                    "l2": "inputs larger than L2 (8 vector blocks x 134 MB)",
                    "parallelism": f"replicas x{world} (independent random vectors)"},
-        "roofline": {"bound": "alu", "kernel": "kpm_sym_kernel (FP64 doubling KPM step)",
-                     "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP64_PEAK_TFLOPS,
-                     "traffic": _profiled_traffic("kg_kernels.cu", "kpm_sym_kernel_msd_sheet_2M.md"),
-                     "algorithmic_bytes": bytes_per_launch,
-                     "peak_source": "nominal FP64 of the profiling recipe (DFMA probe: 1.20)",
-                     "avg_launch_ms": kpm_launch_ms,
-                     "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak,
-                             "frac": achieved_gbs / hbm_peak, "peak_source": "MEASURED_PEAKS.json"
-                             if "hbm_gbs" in peaks else "fallback"}},
+        "roofline": roofline,
         "executed_site_updates_per_s": executed,
         "gpu_launches": int(cnt["kpm_launches"] + cnt["evolve_launches"] + cnt["other_launches"]),
         "phase_ms": {"kpm": cnt["kpm_ms"], "evolve": cnt["evolve_ms"]},
@@ -310,7 +323,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(out_host.numel() * 16 / K), "seconds": e2e_s},
         "sanity_bounded_moments": ok,
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and CONFIG_NAME == DEFAULT_WORKLOAD:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -324,7 +337,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     args = ap.parse_args()
+    global CELLS, VAC, R, M, DT, PREC, CONFIG_NAME
+    CELLS, VAC, R, M, DT, PREC = WORKLOADS[args.workload]
+    CONFIG_NAME = args.workload
     if args.warmup < 1 or args.steps < 1:
         raise SystemExit("--steps and --warmup must be >= 1")
     if args.impl == "reference":

@@ -164,32 +164,34 @@ static kg_status ensure_partials(kg_hamiltonian* h, int R, int grid) {
 //   buffers b0, b1: scratch vector blocks; phi_r is not modified.
 //   mu: device [R][r_stride] double2, moments written at mu[r*r_stride + n], n < M.
 // ---------------------------------------------------------------------------------
-static kg_status kpm_moments(kg_hamiltonian* h, int R, int M, bool sym, const double2* phi_l,
-                             const double2* phi_r, double2* b0, double2* b1, double2* mu,
+template <typename T>
+static kg_status kpm_moments(kg_hamiltonian* h, int R, int M, bool sym, const vec2_t<T>* phi_l,
+                             const vec2_t<T>* phi_r, vec2_t<T>* b0, vec2_t<T>* b1, double2* mu,
                              int64_t r_stride) {
+    using V2 = vec2_t<T>;
     PhaseTimer t(h, 0);
-    const int grid = kpm_grid(h->dev, R, sym);
+    const int grid = kpm_grid<T>(h->dev, R, sym);
     KG_TRY(ensure_partials(h, R, grid));
     double* pf = (double*)h->part_first.p;
     double* ring = (double*)h->part_ring.p;
     cudaStream_t s = h->stream;
     // first step: phi_1 = H~ phi_0 (into b1), moments 0 and 1
-    if (sym) KG_CUDA_TRY(launch_kpm_sym(h->dev, R, true, phi_r, nullptr, b1, pf, grid, s));
-    else KG_CUDA_TRY(launch_kpm_gen(h->dev, R, true, phi_l, phi_r, nullptr, b1, pf, grid, s));
+    if (sym) KG_CUDA_TRY(launch_kpm_sym<T>(h->dev, R, true, phi_r, nullptr, b1, pf, grid, s));
+    else KG_CUDA_TRY(launch_kpm_gen<T>(h->dev, R, true, phi_l, phi_r, nullptr, b1, pf, grid, s));
     KG_CUDA_TRY(launch_reduce_first(pf, grid, R, sym, mu, r_stride, M, s));
     h->counters.kpm_launches += 1;
     h->counters.other_launches += 1;
     h->counters.kpm_site_steps += (double)h->n * R;
     // remaining steps n = 1..S: phi_{n+1} = 2H~phi_n - phi_{n-1}
     const int steps = sym ? (M - 1) / 2 : M - 2;
-    const double2* cur = b1;
-    const double2* prev = phi_r;
-    double2* out = b0;
+    const V2* cur = b1;
+    const V2* prev = phi_r;
+    V2* out = b0;
     int pending = 0, first_pending = 1;
     for (int n = 1; n <= steps; n++) {
         double* slab = ring + (int64_t)((n - 1) % kRing) * grid * R * 2;
-        if (sym) KG_CUDA_TRY(launch_kpm_sym(h->dev, R, false, cur, prev, out, slab, grid, s));
-        else KG_CUDA_TRY(launch_kpm_gen(h->dev, R, false, phi_l, cur, prev, out, slab, grid, s));
+        if (sym) KG_CUDA_TRY(launch_kpm_sym<T>(h->dev, R, false, cur, prev, out, slab, grid, s));
+        else KG_CUDA_TRY(launch_kpm_gen<T>(h->dev, R, false, phi_l, cur, prev, out, slab, grid, s));
         h->counters.kpm_launches += 1;
         h->counters.kpm_site_steps += (double)h->n * R;
         pending++;
@@ -201,9 +203,9 @@ static kg_status kpm_moments(kg_hamiltonian* h, int R, int M, bool sym, const do
             pending = 0;
         }
         // rotate: the new phi_n is `out`; phi_{n-1} becomes the next output (in place)
-        const double2* new_cur = out;
+        const V2* new_cur = out;
         prev = cur;
-        out = const_cast<double2*>(cur);
+        out = const_cast<V2*>(cur);
         cur = new_cur;
     }
     return KG_OK;
@@ -241,14 +243,15 @@ static void term_coef(const Series& ser, int m, int s, double* cr, double* ci) {
 //   p1[k], accumulators acc[k]; xc: commutator chain of the last plain chain with
 //   buffers q1, q0 (q0 receives q_2), routed to qacc (null = acc[0]).
 // The plain-chain inputs are overwritten from m = 2 on (p_m replaces p_{m-2}).
+template <typename T>
 static kg_status run_series(kg_hamiltonian* h, int R, const Series& ser, int s, int nch, bool xc,
-                            double2* const* in, double2* const* p1, double2* const* acc,
-                            double2* q1, double2* q0, double2* qacc) {
+                            vec2_t<T>* const* in, vec2_t<T>* const* p1, vec2_t<T>* const* acc,
+                            vec2_t<T>* q1, vec2_t<T>* q0, vec2_t<T>* qacc) {
+    using V2 = vec2_t<T>;
     PhaseTimer t(h, 1);
-    const int grid = stream_grid(h->n * R);
-    Chains ch;
-    double2* cur[3];
-    double2* prv[3];
+    ChainsT<T> ch;
+    V2* cur[3];
+    V2* prv[3];
     for (int k = 0; k < nch; k++) {
         ch.cur[k] = in[k];
         ch.nxt[k] = p1[k];
@@ -263,12 +266,12 @@ static kg_status run_series(kg_hamiltonian* h, int R, const Series& ser, int s, 
     double cr = 0, ci = 0;
     if (ser.np > 1) term_coef(ser, 1, s, &cr, &ci);
     // first step: p_1 = H~ p_0, acc = J_0 p_0 + c_1 p_1 (c_1 = 0 when N_p = 1)
-    KG_CUDA_TRY(launch_evolve(h->dev, R, nch, xc, true, ser.j[0], cr, ci, ch, grid, h->stream));
+    KG_CUDA_TRY(launch_evolve<T>(h->dev, R, nch, xc, true, ser.j[0], cr, ci, ch, h->stream));
     h->counters.evolve_launches += 1;
     h->counters.evolve_site_steps += (double)h->n * R * (nch + (xc ? 1 : 0));
-    double2* qc = q1;
-    double2* qp = nullptr;
-    double2* qn = q0;
+    V2* qc = q1;
+    V2* qp = nullptr;
+    V2* qn = q0;
     for (int m = 2; m < ser.np; m++) {
         term_coef(ser, m, s, &cr, &ci);
         for (int k = 0; k < nch; k++) {
@@ -281,21 +284,118 @@ static kg_status run_series(kg_hamiltonian* h, int R, const Series& ser, int s, 
             ch.qprev = qp;
             ch.qnxt = qn;
         }
-        KG_CUDA_TRY(launch_evolve(h->dev, R, nch, xc, false, 0.0, cr, ci, ch, grid, h->stream));
+        KG_CUDA_TRY(launch_evolve<T>(h->dev, R, nch, xc, false, 0.0, cr, ci, ch, h->stream));
         h->counters.evolve_launches += 1;
         h->counters.evolve_site_steps += (double)h->n * R * (nch + (xc ? 1 : 0));
         for (int k = 0; k < nch; k++) {
-            double2* t2 = prv[k];
+            V2* t2 = prv[k];
             prv[k] = cur[k];
             cur[k] = t2;
         }
         if (xc) {
             // q_m now sits in qn; q_{m+1} will overwrite q_{m-1}
-            double2* newc = qn;
+            V2* newc = qn;
             qp = qc;
             qc = newc;
             qn = qp;
         }
+    }
+    return KG_OK;
+}
+
+// Typed view of workspace vector block k.
+template <typename T>
+static vec2_t<T>* VT(kg_hamiltonian* h, int k) { return (vec2_t<T>*)h->vec[k].p; }
+
+// Stages the caller's complex128 vectors (host or device) into block `dst` of
+// precision T; `tmp` is a scratch block used for the complex64 conversion.
+template <typename T>
+static kg_status stage_input(kg_hamiltonian* h, const double* phi, int R, int dst, int tmp) {
+    if constexpr (sizeof(T) == sizeof(double)) {
+        (void)tmp;
+        return copy_in(h, phi, V(h, dst), R);
+    } else {
+        KG_TRY(copy_in(h, phi, V(h, tmp), R));
+        KG_CUDA_TRY(launch_to_c64(V(h, tmp), VT<float>(h, dst), h->n * R, h->stream));
+        h->counters.other_launches += 1;
+        // the zero row of the complex64 layout
+        KG_CUDA_TRY(cudaMemsetAsync(VT<float>(h, dst) + h->n * R, 0, (size_t)R * sizeof(float2), h->stream));
+        return KG_OK;
+    }
+}
+
+// Zero rows of the complex64 layout for the listed blocks (ensure_vectors clears the
+// complex128 position of row n, which is a different byte offset).
+template <typename T>
+static kg_status clear_zero_rows(kg_hamiltonian* h, int R, int count) {
+    if constexpr (sizeof(T) != sizeof(double)) {
+        for (int k = 0; k < count; k++)
+            KG_CUDA_TRY(cudaMemsetAsync(VT<T>(h, k) + h->n * R, 0, (size_t)R * sizeof(vec2_t<T>), h->stream));
+    }
+    return KG_OK;
+}
+
+template <typename T>
+static kg_status dos_impl(kg_hamiltonian* h, int R, int M, const double* phi) {
+    KG_TRY(ensure_vectors(h, R, 4));
+    KG_TRY(clear_zero_rows<T>(h, R, 4));
+    KG_TRY(stage_input<T>(h, phi, R, 0, 3));
+    return kpm_moments<T>(h, R, M, true, VT<T>(h, 0), VT<T>(h, 0), VT<T>(h, 1), VT<T>(h, 2),
+                          (double2*)h->moments.p, M);
+}
+
+template <typename T>
+static kg_status vac_impl(kg_hamiltonian* h, int R, int M, int NC, const Series& ser, const double* phi) {
+    using V2 = vec2_t<T>;
+    // blocks: 0 A, 1 B, 2 A', 3 B', 4 L, 5 p1(A), 6 p1(B), 7 kpm b0, 8 kpm b1
+    KG_TRY(ensure_vectors(h, R, 9));
+    KG_TRY(clear_zero_rows<T>(h, R, 9));
+    V2 *A = VT<T>(h, 0), *B = VT<T>(h, 1), *A2 = VT<T>(h, 2), *B2 = VT<T>(h, 3), *L = VT<T>(h, 4);
+    const double vscale = h->emax / kHbarEvFs;
+    KG_TRY(stage_input<T>(h, phi, R, 0, 7));
+    KG_CUDA_TRY(launch_apply<T>(h->dev, R, 2, vscale, A, B, h->stream));   // B = V phi
+    h->counters.other_launches += 1;
+    double2* mu = (double2*)h->moments.p;
+    for (int t = 0; t < NC; t++) {
+        if (t > 0) {
+            // A <- U(-dt) A, B <- U(-dt) B  (Eqs. 42-43)
+            V2* in[2] = {A, B};
+            V2* p1[2] = {VT<T>(h, 5), VT<T>(h, 6)};
+            V2* acc[2] = {A2, B2};
+            KG_TRY(run_series<T>(h, R, ser, +1, 2, false, in, p1, acc, nullptr, nullptr, nullptr));
+            std::swap(A, A2);
+            std::swap(B, B2);
+        }
+        KG_CUDA_TRY(launch_apply<T>(h->dev, R, 2, vscale, A, L, h->stream));   // L = V A
+        h->counters.other_launches += 1;
+        KG_TRY(kpm_moments<T>(h, R, M, false, L, B, VT<T>(h, 7), VT<T>(h, 8), mu + (int64_t)t * M,
+                              (int64_t)NC * M));
+    }
+    return KG_OK;
+}
+
+template <typename T>
+static kg_status msd_impl(kg_hamiltonian* h, int R, int M, int NC, const Series& ser, const double* phi) {
+    using V2 = vec2_t<T>;
+    // blocks: 0 psi, 1 xi, 2 psi', 3 xi', 4 p1(xi), 5 p1(psi), 6 q1, 7 q0
+    KG_TRY(ensure_vectors(h, R, 8));
+    KG_TRY(clear_zero_rows<T>(h, R, 8));
+    V2 *psi = VT<T>(h, 0), *xi = VT<T>(h, 1), *psi2 = VT<T>(h, 2), *xi2 = VT<T>(h, 3);
+    KG_TRY(stage_input<T>(h, phi, R, 0, 7));
+    KG_CUDA_TRY(cudaMemsetAsync(xi, 0, vec_bytes(h, R), h->stream));   // [X, U(0)] = 0
+    double2* mu = (double2*)h->moments.p;
+    KG_CUDA_TRY(cudaMemsetAsync(mu, 0, (size_t)R * NC * M * sizeof(double2), h->stream));
+    for (int t = 1; t < NC; t++) {
+        // xi <- U(dt) xi + [X, U(dt)] psi ;  psi <- U(dt) psi  (Eq. 44)
+        V2* in[2] = {xi, psi};
+        V2* p1[2] = {VT<T>(h, 4), VT<T>(h, 5)};
+        V2* acc[2] = {xi2, psi2};
+        KG_TRY(run_series<T>(h, R, ser, -1, 2, true, in, p1, acc, VT<T>(h, 6), VT<T>(h, 7), nullptr));
+        std::swap(xi, xi2);
+        std::swap(psi, psi2);
+        // moments of xi; scratch: the now-free chain buffers 4 and 5
+        KG_TRY(kpm_moments<T>(h, R, M, true, xi, xi, VT<T>(h, 4), VT<T>(h, 5), mu + (int64_t)t * M,
+                              (int64_t)NC * M));
     }
     return KG_OK;
 }
@@ -306,7 +406,6 @@ static kg_status check_run(const kg_hamiltonian* h, const kg_run* run, bool need
     if (run->n_moments < 1) return fail(KG_EINVAL, "n_moments must be >= 1");
     if (!valid_r(run->n_vectors)) return fail(KG_EINVAL, "n_vectors must be a power of two in 1..64");
     if (run->precision != KG_FP64 && run->precision != KG_C64) return fail(KG_EINVAL, "unknown precision");
-    if (run->precision == KG_C64) return fail(KG_EINVAL, "precision KG_C64 is not available in this build");
     if (need_time && run->n_times < 1) return fail(KG_EINVAL, "n_times must be >= 1");
     return KG_OK;
 }
@@ -435,10 +534,9 @@ kg_status kg_dos_moments(kg_hamiltonian* h, const kg_run* run, const double* phi
     if (!phi || !mu_out) return fail(KG_EINVAL, "phi and mu_out must not be NULL");
     KG_TRY(check_device(h));
     const int R = run->n_vectors, M = run->n_moments;
-    KG_TRY(ensure_vectors(h, R, 3));
     KG_TRY(ensure_moments(h, (size_t)R * M));
-    KG_TRY(copy_in(h, phi, V(h, 0), R));
-    KG_TRY(kpm_moments(h, R, M, true, V(h, 0), V(h, 0), V(h, 1), V(h, 2), (double2*)h->moments.p, M));
+    if (run->precision == KG_C64) KG_TRY(dos_impl<float>(h, R, M, phi));
+    else KG_TRY(dos_impl<double>(h, R, M, phi));
     return copy_out(h, h->moments.p, mu_out, (size_t)R * M * sizeof(double2));
 }
 
@@ -450,32 +548,10 @@ kg_status kg_vac(kg_hamiltonian* h, const kg_run* run, const double* phi, double
     const int R = run->n_vectors, M = run->n_moments, NC = run->n_times;
     Series ser;
     if (NC > 1) KG_TRY(series_for(h, run->dt, run->bessel_tol, &ser));
-    // vectors: 0 A, 1 B, 2 A', 3 B', 4 L, 5 p1(A), 6 p1(B), 7 kpm b0, 8 kpm b1
-    KG_TRY(ensure_vectors(h, R, 9));
     KG_TRY(ensure_moments(h, (size_t)R * NC * M));
-    double2 *A = V(h, 0), *B = V(h, 1), *A2 = V(h, 2), *B2 = V(h, 3), *L = V(h, 4);
-    const int grid = stream_grid(h->n * R);
-    const double vscale = h->emax / kHbarEvFs;
-    KG_TRY(copy_in(h, phi, A, R));
-    KG_CUDA_TRY(launch_apply(h->dev, R, 2, vscale, A, B, grid, h->stream));   // B = V phi
-    h->counters.other_launches += 1;
-    double2* mu = (double2*)h->moments.p;
-    for (int t = 0; t < NC; t++) {
-        if (t > 0) {
-            // A <- U(-dt) A, B <- U(-dt) B  (Eqs. 42-43)
-            double2* in[2] = {A, B};
-            double2* p1[2] = {V(h, 5), V(h, 6)};
-            double2* acc[2] = {A2, B2};
-            KG_TRY(run_series(h, R, ser, +1, 2, false, in, p1, acc, nullptr, nullptr, nullptr));
-            std::swap(A, A2);
-            std::swap(B, B2);
-        }
-        KG_CUDA_TRY(launch_apply(h->dev, R, 2, vscale, A, L, grid, h->stream));   // L = V A
-        h->counters.other_launches += 1;
-        KG_TRY(kpm_moments(h, R, M, false, L, B, V(h, 7), V(h, 8), mu + (int64_t)t * M,
-                           (int64_t)NC * M));
-    }
-    return copy_out(h, mu, mu_out, (size_t)R * NC * M * sizeof(double2));
+    if (run->precision == KG_C64) KG_TRY(vac_impl<float>(h, R, M, NC, ser, phi));
+    else KG_TRY(vac_impl<double>(h, R, M, NC, ser, phi));
+    return copy_out(h, h->moments.p, mu_out, (size_t)R * NC * M * sizeof(double2));
 }
 
 kg_status kg_msd(kg_hamiltonian* h, const kg_run* run, const double* phi, double* mu_out) {
@@ -486,27 +562,10 @@ kg_status kg_msd(kg_hamiltonian* h, const kg_run* run, const double* phi, double
     const int R = run->n_vectors, M = run->n_moments, NC = run->n_times;
     Series ser;
     if (NC > 1) KG_TRY(series_for(h, run->dt, run->bessel_tol, &ser));
-    // vectors: 0 psi, 1 xi, 2 psi', 3 xi', 4 p1(xi), 5 p1(psi), 6 q1, 7 q0
-    KG_TRY(ensure_vectors(h, R, 8));
     KG_TRY(ensure_moments(h, (size_t)R * NC * M));
-    double2 *psi = V(h, 0), *xi = V(h, 1), *psi2 = V(h, 2), *xi2 = V(h, 3);
-    KG_TRY(copy_in(h, phi, psi, R));
-    KG_CUDA_TRY(cudaMemsetAsync(xi, 0, vec_bytes(h, R), h->stream));   // [X, U(0)] = 0
-    double2* mu = (double2*)h->moments.p;
-    KG_CUDA_TRY(cudaMemsetAsync(mu, 0, (size_t)R * NC * M * sizeof(double2), h->stream));
-    for (int t = 1; t < NC; t++) {
-        // xi <- U(dt) xi + [X, U(dt)] psi ;  psi <- U(dt) psi  (Eq. 44)
-        double2* in[2] = {xi, psi};
-        double2* p1[2] = {V(h, 4), V(h, 5)};
-        double2* acc[2] = {xi2, psi2};
-        KG_TRY(run_series(h, R, ser, -1, 2, true, in, p1, acc, V(h, 6), V(h, 7), nullptr));
-        std::swap(xi, xi2);
-        std::swap(psi, psi2);
-        // moments of xi; scratch: the now-free chain buffers 4 and 5
-        KG_TRY(kpm_moments(h, R, M, true, xi, xi, V(h, 4), V(h, 5), mu + (int64_t)t * M,
-                           (int64_t)NC * M));
-    }
-    return copy_out(h, mu, mu_out, (size_t)R * NC * M * sizeof(double2));
+    if (run->precision == KG_C64) KG_TRY(msd_impl<float>(h, R, M, NC, ser, phi));
+    else KG_TRY(msd_impl<double>(h, R, M, NC, ser, phi));
+    return copy_out(h, h->moments.p, mu_out, (size_t)R * NC * M * sizeof(double2));
 }
 
 kg_status kg_apply(kg_hamiltonian* h, int op, const double* in_dev, double* out_dev, int n_vectors) {
@@ -519,8 +578,7 @@ kg_status kg_apply(kg_hamiltonian* h, int op, const double* in_dev, double* out_
     const int R = n_vectors;
     KG_TRY(ensure_vectors(h, R, 2));
     KG_TRY(copy_in(h, in_dev, V(h, 0), R));
-    KG_CUDA_TRY(launch_apply(h->dev, R, op, h->emax / kHbarEvFs, V(h, 0), V(h, 1),
-                             stream_grid(h->n * R), h->stream));
+    KG_CUDA_TRY(launch_apply<double>(h->dev, R, op, h->emax / kHbarEvFs, V(h, 0), V(h, 1), h->stream));
     h->counters.other_launches += 1;
     return copy_out(h, V(h, 1), out_dev, (size_t)h->n * R * sizeof(double2));
 }
@@ -543,11 +601,11 @@ kg_status kg_evolve(kg_hamiltonian* h, double dt, int which, double bessel_tol, 
     double2* p1[1] = {V(h, 1)};
     double2* acc[1] = {V(h, 2)};
     if (which == KG_U_COMMUTATOR) {
-        KG_TRY(run_series(h, R, ser, -1, 1, true, in, p1, acc, V(h, 3), V(h, 4), V(h, 5)));
+        KG_TRY(run_series<double>(h, R, ser, -1, 1, true, in, p1, acc, V(h, 3), V(h, 4), V(h, 5)));
         return copy_out(h, V(h, 5), out_dev, (size_t)h->n * R * sizeof(double2));
     }
-    KG_TRY(run_series(h, R, ser, which == KG_U_FORWARD ? -1 : +1, 1, false, in, p1, acc, nullptr,
-                      nullptr, nullptr));
+    KG_TRY(run_series<double>(h, R, ser, which == KG_U_FORWARD ? -1 : +1, 1, false, in, p1, acc, nullptr,
+                              nullptr, nullptr));
     return copy_out(h, V(h, 2), out_dev, (size_t)h->n * R * sizeof(double2));
 }
 

@@ -74,19 +74,37 @@ struct DevH {
 // Number of co-resident 256-thread CTAs per SM for a kernel, and the SM count.
 int sm_count();
 
+// Complex vector element of each precision.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<double> { using type = double2; };
+template <>
+struct Vec2<float> { using type = float2; };
+template <typename T>
+using vec2_t = typename Vec2<T>::type;
+
 // ----- launchers (kg_kernels.cu); all return cudaError_t of the launch -----
+// T = double: complex128 vectors (KG_FP64); T = float: complex64 vectors (KG_C64).
+// Partial sums and moments are FP64 in both.
 
 // KPM step with phi_L = phi_R (Chebyshev doubling): out = c H~ cur - prev (prev may be
 // null on the first step, then c = 1), partial[g][r][2] = (sum |cur|^2, sum Re conj(out) cur).
-cudaError_t launch_kpm_sym(const DevH& H, int R, bool first, const double2* cur,
-                           const double2* prev, double2* out, double* partial, int grid,
+template <typename T>
+cudaError_t launch_kpm_sym(const DevH& H, int R, bool first, const vec2_t<T>* cur,
+                           const vec2_t<T>* prev, vec2_t<T>* out, double* partial, int grid,
                            cudaStream_t s);
 
 // KPM step with a separate phi_L: out = c H~ cur - prev; partial[g][r][2] = <L|out>.
 // On the first step partial[g][r][4] = (<L|out>, <L|cur>).
-cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const double2* L,
-                           const double2* cur, const double2* prev, double2* out,
+template <typename T>
+cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const vec2_t<T>* L,
+                           const vec2_t<T>* cur, const vec2_t<T>* prev, vec2_t<T>* out,
                            double* partial, int grid, cudaStream_t s);
+
+// One full resident wave of the (non-first) KPM step kernel for this H and R.
+template <typename T>
+int kpm_grid(const DevH& H, int R, bool sym);
 
 // Reduce per-block partials of a KPM run into moments mu[r * r_stride + n].
 //   first: partial [grid][R][A] of the first step (A = 2 sym, 4 gen)
@@ -97,30 +115,36 @@ cudaError_t launch_reduce_ring(const double* ring, int slab0, int nslab, int rin
                                int grid, int R, bool sym, int n0, double2* mu,
                                int64_t r_stride, int M, cudaStream_t s);
 
-struct Chains {
-    const double2* cur[3] = {nullptr, nullptr, nullptr};
-    const double2* prev[3] = {nullptr, nullptr, nullptr};
-    double2* nxt[3] = {nullptr, nullptr, nullptr};
-    double2* acc[3] = {nullptr, nullptr, nullptr};
+template <typename T>
+struct ChainsT {
+    using V2 = vec2_t<T>;
+    const V2* cur[3] = {nullptr, nullptr, nullptr};
+    const V2* prev[3] = {nullptr, nullptr, nullptr};
+    V2* nxt[3] = {nullptr, nullptr, nullptr};
+    V2* acc[3] = {nullptr, nullptr, nullptr};
     // commutator chain [X, T_m(H~)] applied to chain nch-1
-    const double2* qcur = nullptr;
-    const double2* qprev = nullptr;
-    double2* qnxt = nullptr;
-    double2* qacc = nullptr;        // null: accumulate into acc[0]
+    const V2* qcur = nullptr;
+    const V2* qprev = nullptr;
+    V2* qnxt = nullptr;
+    V2* qacc = nullptr;             // null: accumulate into acc[0]
 };
 
 // One term m of the Chebyshev-Bessel series on nch plain chains (+ the commutator
-// chain when xc).  first = the m = 1 step (also adds the J_0 term).
+// chain when xc).  first = the m = 1 step (also adds the J_0 term).  The grid is one
+// resident wave of the selected kernel.
+template <typename T>
 cudaError_t launch_evolve(const DevH& H, int R, int nch, bool xc, bool first, double j0,
-                          double cr, double ci, const Chains& ch, int grid, cudaStream_t s);
+                          double cr, double ci, const ChainsT<T>& ch, cudaStream_t s);
 
 // out = op(in): 0 H~, 1 [X, H~], 2 V = -(i E_max / hbar)[X, H~] (scale = E_max / hbar).
-cudaError_t launch_apply(const DevH& H, int R, int op, double scale, const double2* in,
-                         double2* out, int grid, cudaStream_t s);
+template <typename T>
+cudaError_t launch_apply(const DevH& H, int R, int op, double scale, const vec2_t<T>* in,
+                         vec2_t<T>* out, cudaStream_t s);
+
+// complex128 -> complex64, element-wise.
+cudaError_t launch_to_c64(const double2* in, float2* out, int64_t n_items, cudaStream_t s);
 
 // Grid size (CTAs) for a streaming kernel over n_items = n * R complex items.
 int stream_grid(int64_t n_items);
-// One full resident wave of the (non-first) KPM step kernel for this H and R.
-int kpm_grid(const DevH& H, int R, bool sym);
 
 }  // namespace kg

@@ -1,4 +1,8 @@
-// FP64 kernels of the Chebyshev recursion for sm_103a.
+// Kernels of the Chebyshev recursion for sm_103a, in two precisions:
+//   T = double: complex128 vectors, FP64 arithmetic and FP64 inner products;
+//   T = float:  complex64 vectors, FP32 recursion, inner products accumulated per
+//               thread with exact FP32 products and compensated (TwoSum) sums, then
+//               combined across threads and blocks in FP64.
 //
 // Every kernel streams over the N*R complex items of a block of R vectors laid out
 // [N+1][R] (row N is a permanent zero row; the neighbour table points removed or
@@ -7,10 +11,10 @@
 // R vectors of a site share one load of the site's three neighbour indices.
 //
 // The GB300 executes FP64 at 1/64 of the FP32 rate (about 0.6e12 DFMA/s, and DADD
-// slower than DFMA), so the recursion is limited by the DP pipe, not by HBM.  The
-// kernels therefore express every FP64 operation as a fused multiply-add:
-// the neighbour sum and the "- T_{n-1}" are folded into the hopping multiply
-// (3 DFMA per real component), and each inner product costs 2 DFMA per component.
+// slower than DFMA), so the FP64 recursion is limited by the DP pipe, not by HBM.
+// FP64 operations are therefore all fused multiply-adds: the neighbour sum and the
+// "- T_{n-1}" fold into the hopping multiply (3 FMA per real component), and each
+// inner product costs 2 FMA per component.  The FP32 kernels are HBM-bound.
 #include <cuda_runtime.h>
 
 #include <unordered_map>
@@ -23,7 +27,39 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
 // --------------------------------------------------------------------------------
-// Block reduction of NACC per-thread accumulators belonging to vector r = tid % R.
+// Inner-product accumulators
+// --------------------------------------------------------------------------------
+
+template <typename T>
+struct Acc;
+
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+// FP32 products are split exactly into p + e (e = fma(a, b, -p)); p is added with
+// Knuth's TwoSum, whose rounding error joins e in the compensation term c.  The
+// explicit-rounding intrinsics keep the compiler from contracting or reassociating.
+template <>
+struct Acc<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = fmaf(a, b, -p);
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        c = __fadd_rn(c, __fadd_rn(err, e));
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// --------------------------------------------------------------------------------
+// Block reduction of NACC per-thread FP64 partials belonging to vector r = tid % R.
 // Deterministic: fixed shuffle tree, then a fixed-order sum over warps.
 // dst receives [R][NACC] doubles for this block.
 // --------------------------------------------------------------------------------
@@ -59,15 +95,16 @@ __device__ __forceinline__ void block_reduce(double (&acc)[NACC], double* __rest
     }
 }
 
+template <typename T>
 struct Nbr {
-    double2 a, b, c, x;   // the three neighbours and the site itself
+    vec2_t<T> a, b, c, x;   // the three neighbours and the site itself
 };
 
-template <int R>
-__device__ __forceinline__ Nbr gather(const int32_t* __restrict__ idx, int64_t istride, int64_t n,
-                                      int r, const double2* __restrict__ v) {
+template <typename T, int R>
+__device__ __forceinline__ Nbr<T> gather(const int32_t* __restrict__ idx, int64_t istride, int64_t n,
+                                         int r, const vec2_t<T>* __restrict__ v) {
     const int32_t i0 = __ldg(idx + n), i1 = __ldg(idx + istride + n), i2 = __ldg(idx + 2 * istride + n);
-    Nbr g;
+    Nbr<T> g;
     g.a = __ldg(v + (int64_t)i0 * R + r);
     g.b = __ldg(v + (int64_t)i1 * R + r);
     g.c = __ldg(v + (int64_t)i2 * R + r);
@@ -76,11 +113,18 @@ __device__ __forceinline__ Nbr gather(const int32_t* __restrict__ idx, int64_t i
 }
 
 // y = c * (a + b + c3) + e * x - z   as a chain of fused multiply-adds (z may be 0).
-__device__ __forceinline__ double hop(double c, double a, double b, double c3, double e, double x,
-                                      double z, bool onsite) {
-    double t = onsite ? fma(e, x, -z) : -z;
+template <typename T>
+__device__ __forceinline__ T hop(T c, T a, T b, T c3, T e, T x, T z, bool onsite) {
+    T t = onsite ? fma(e, x, -z) : -z;
     return fma(c, a, fma(c, b, fma(c, c3, t)));
 }
+
+template <typename T>
+__device__ __forceinline__ vec2_t<T> mk(T x, T y);
+template <>
+__device__ __forceinline__ double2 mk<double>(double x, double y) { return make_double2(x, y); }
+template <>
+__device__ __forceinline__ float2 mk<float>(float x, float y) { return make_float2(x, y); }
 
 // --------------------------------------------------------------------------------
 // KPM step with phi_L = phi_R (DOS and MSD moments).  Uses the Chebyshev product
@@ -89,28 +133,31 @@ __device__ __forceinline__ double hop(double c, double a, double b, double c3, d
 // (both real for Hermitian H~).  The kernel computes phi_{n+1} = 2H~phi_n - phi_{n-1}
 // (first step: phi_1 = H~ phi_0) and the two per-block partial sums.
 // --------------------------------------------------------------------------------
-template <int R, bool ONSITE, bool FIRST>
-__global__ void __launch_bounds__(kThreads) kpm_sym_kernel(DevH H, const double2* __restrict__ cur,
-                                                           const double2* prev, double2* out,
+template <typename T, int R, bool ONSITE, bool FIRST>
+__global__ void __launch_bounds__(kThreads) kpm_sym_kernel(DevH H, const vec2_t<T>* __restrict__ cur,
+                                                           const vec2_t<T>* prev, vec2_t<T>* out,
                                                            double* __restrict__ partial) {
     const int64_t n_items = H.n * R;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     const int r = threadIdx.x & (R - 1);
-    const double c = FIRST ? H.h : 2.0 * H.h;
-    double acc[2] = {0.0, 0.0};
+    const T c = (T)(FIRST ? H.h : 2.0 * H.h);
+    Acc<T> a0, a1;
     for (int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x; w < n_items; w += stride) {
         const int64_t n = w / R;
-        const Nbr g = gather<R>(H.idx, H.istride, n, r, cur);
-        double e = 0.0;
-        if constexpr (ONSITE) e = (FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n);
-        double2 z = make_double2(0.0, 0.0);
+        const Nbr<T> g = gather<T, R>(H.idx, H.istride, n, r, cur);
+        T e = 0;
+        if constexpr (ONSITE) e = (T)((FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n));
+        vec2_t<T> z = mk<T>(0, 0);
         if constexpr (!FIRST) z = prev[w];
-        const double yr = hop(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
-        const double yi = hop(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
-        out[w] = make_double2(yr, yi);
-        acc[0] = fma(g.x.x, g.x.x, fma(g.x.y, g.x.y, acc[0]));
-        acc[1] = fma(yr, g.x.x, fma(yi, g.x.y, acc[1]));
+        const T yr = hop<T>(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
+        const T yi = hop<T>(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
+        out[w] = mk<T>(yr, yi);
+        a0.add_prod(g.x.x, g.x.x);
+        a0.add_prod(g.x.y, g.x.y);
+        a1.add_prod(yr, g.x.x);
+        a1.add_prod(yi, g.x.y);
     }
+    double acc[2] = {a0.value(), a1.value()};
     block_reduce<R, 2>(acc, partial + (int64_t)blockIdx.x * R * 2);
 }
 
@@ -119,37 +166,43 @@ __global__ void __launch_bounds__(kThreads) kpm_sym_kernel(DevH H, const double2
 //   phi_{n+1} = 2H~phi_n - phi_{n-1};  C_{n+1} = <phi_L|phi_{n+1}>
 // First step: phi_1 = H~ phi_0 and partials (<L|phi_1>, <L|phi_0>).
 // --------------------------------------------------------------------------------
-template <int R, bool ONSITE, bool FIRST>
-__global__ void __launch_bounds__(kThreads) kpm_gen_kernel(DevH H, const double2* __restrict__ L,
-                                                           const double2* __restrict__ cur,
-                                                           const double2* prev, double2* out,
+template <typename T, int R, bool ONSITE, bool FIRST>
+__global__ void __launch_bounds__(kThreads) kpm_gen_kernel(DevH H, const vec2_t<T>* __restrict__ L,
+                                                           const vec2_t<T>* __restrict__ cur,
+                                                           const vec2_t<T>* prev, vec2_t<T>* out,
                                                            double* __restrict__ partial) {
     constexpr int NACC = FIRST ? 4 : 2;
     const int64_t n_items = H.n * R;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     const int r = threadIdx.x & (R - 1);
-    const double c = FIRST ? H.h : 2.0 * H.h;
-    double acc[NACC];
-#pragma unroll
-    for (int q = 0; q < NACC; q++) acc[q] = 0.0;
+    const T c = (T)(FIRST ? H.h : 2.0 * H.h);
+    Acc<T> a[NACC];
     for (int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x; w < n_items; w += stride) {
         const int64_t n = w / R;
-        const Nbr g = gather<R>(H.idx, H.istride, n, r, cur);
-        double e = 0.0;
-        if constexpr (ONSITE) e = (FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n);
-        double2 z = make_double2(0.0, 0.0);
+        const Nbr<T> g = gather<T, R>(H.idx, H.istride, n, r, cur);
+        T e = 0;
+        if constexpr (ONSITE) e = (T)((FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n));
+        vec2_t<T> z = mk<T>(0, 0);
         if constexpr (!FIRST) z = prev[w];
-        const double yr = hop(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
-        const double yi = hop(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
-        out[w] = make_double2(yr, yi);
-        const double2 l = __ldg(L + w);
-        acc[0] = fma(l.x, yr, fma(l.y, yi, acc[0]));
-        acc[1] = fma(l.x, yi, fma(-l.y, yr, acc[1]));
+        const T yr = hop<T>(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
+        const T yi = hop<T>(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
+        out[w] = mk<T>(yr, yi);
+        const vec2_t<T> l = __ldg(L + w);
+        // <L|y> = (l.x y.x + l.y y.y) + i (l.x y.y - l.y y.x)
+        a[0].add_prod(l.x, yr);
+        a[0].add_prod(l.y, yi);
+        a[1].add_prod(l.x, yi);
+        a[1].add_prod(-l.y, yr);
         if constexpr (FIRST) {
-            acc[2] = fma(l.x, g.x.x, fma(l.y, g.x.y, acc[2]));
-            acc[3] = fma(l.x, g.x.y, fma(-l.y, g.x.x, acc[3]));
+            a[2].add_prod(l.x, g.x.x);
+            a[2].add_prod(l.y, g.x.y);
+            a[3].add_prod(l.x, g.x.y);
+            a[3].add_prod(-l.y, g.x.x);
         }
     }
+    double acc[NACC];
+#pragma unroll
+    for (int q = 0; q < NACC; q++) acc[q] = a[q].value();
     block_reduce<R, NACC>(acc, partial + (int64_t)blockIdx.x * R * NACC);
 }
 
@@ -232,8 +285,8 @@ __global__ void reduce_ring_kernel(const double* __restrict__ ring, int slab0, i
 // --------------------------------------------------------------------------------
 // (s i)^m is real for even m and imaginary for odd m, so ODD selects the two FMAs that
 // the non-zero part of the coefficient needs: acc += cr * y  or  acc += i ci * y.
-__device__ __forceinline__ void add_term(double2& a, bool odd, double cr, double ci, double yr,
-                                         double yi) {
+template <typename T>
+__device__ __forceinline__ void add_term(vec2_t<T>& a, bool odd, T cr, T ci, T yr, T yi) {
     if (odd) {
         a.x = fma(-ci, yi, a.x);
         a.y = fma(ci, yr, a.y);
@@ -243,72 +296,74 @@ __device__ __forceinline__ void add_term(double2& a, bool odd, double cr, double
     }
 }
 
-template <int R, int NCH, bool XC, bool FIRST, bool ONSITE, bool YPAR, bool ODD>
-__global__ void __launch_bounds__(kThreads) evolve_kernel(DevH H, double j0, double cr, double ci,
-                                                          Chains ch) {
+template <typename T, int R, int NCH, bool XC, bool FIRST, bool ONSITE, bool YPAR, bool ODD>
+__global__ void __launch_bounds__(kThreads) evolve_kernel(DevH H, double j0d, double crd, double cid,
+                                                          ChainsT<T> ch) {
+    using V2 = vec2_t<T>;
     const int64_t n_items = H.n * R;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     const int r = threadIdx.x & (R - 1);
-    const double c = FIRST ? H.h : 2.0 * H.h;
-    const double cx = FIRST ? 1.0 : 2.0;
+    const T c = (T)(FIRST ? H.h : 2.0 * H.h);
+    const T cx = FIRST ? (T)1 : (T)2;
+    const T j0 = (T)j0d, cr = (T)crd, ci = (T)cid;
     const bool q_into_0 = (ch.qacc == nullptr);
     for (int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x; w < n_items; w += stride) {
         const int64_t n = w / R;
-        double e = 0.0;
-        if constexpr (ONSITE) e = (FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n);
-        double2 q_add = make_double2(0.0, 0.0);   // commutator contribution routed to acc_0
-        Nbr gs;
+        T e = 0;
+        if constexpr (ONSITE) e = (T)((FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n));
+        V2 q_add = mk<T>(0, 0);   // chain-0 accumulator, finished after the commutator chain
+        Nbr<T> gs;
 #pragma unroll
         for (int k = 0; k < NCH; k++) {
-            const Nbr g = gather<R>(H.idx, H.istride, n, r, ch.cur[k]);
+            const Nbr<T> g = gather<T, R>(H.idx, H.istride, n, r, ch.cur[k]);
             if (k == NCH - 1) gs = g;
-            double2 z = make_double2(0.0, 0.0);
+            V2 z = mk<T>(0, 0);
             if constexpr (!FIRST) z = ch.prev[k][w];
-            const double yr = hop(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
-            const double yi = hop(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
-            ch.nxt[k][w] = make_double2(yr, yi);
-            double2 a;
+            const T yr = hop<T>(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
+            const T yi = hop<T>(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
+            ch.nxt[k][w] = mk<T>(yr, yi);
+            V2 a;
             if constexpr (FIRST) {
-                a = make_double2(j0 * g.x.x, j0 * g.x.y);
+                a = mk<T>(j0 * g.x.x, j0 * g.x.y);
             } else {
                 a = ch.acc[k][w];
             }
-            add_term(a, ODD, cr, ci, yr, yi);
+            add_term<T>(a, ODD, cr, ci, yr, yi);
             if (k == 0) {
-                q_add = a;   // finish acc_0 after the commutator chain
+                q_add = a;
             } else {
                 ch.acc[k][w] = a;
             }
         }
         if constexpr (XC) {
             // [X,H~] p_{m-1}: sum over slots of (X_n - X_m) H~_nm p[nbr]
-            double d0, d1, d2;
+            double d0d, d1d, d2d;
             if constexpr (YPAR) {
                 const int p = __ldg(H.parity + n);
-                d0 = H.dh[p][0]; d1 = H.dh[p][1]; d2 = H.dh[p][2];
+                d0d = H.dh[p][0]; d1d = H.dh[p][1]; d2d = H.dh[p][2];
             } else {
-                d0 = H.dh[0][0]; d1 = H.dh[0][1]; d2 = H.dh[0][2];
+                d0d = H.dh[0][0]; d1d = H.dh[0][1]; d2d = H.dh[0][2];
             }
-            d0 *= cx; d1 *= cx; d2 *= cx;
-            double qr, qi;
+            const T d0 = cx * (T)d0d, d1 = cx * (T)d1d, d2 = cx * (T)d2d;
+            T qr, qi;
             if constexpr (FIRST) {
                 qr = fma(d0, gs.a.x, fma(d1, gs.b.x, d2 * gs.c.x));
                 qi = fma(d0, gs.a.y, fma(d1, gs.b.y, d2 * gs.c.y));
             } else {
-                const Nbr gq = gather<R>(H.idx, H.istride, n, r, ch.qcur);
-                double2 qz = make_double2(0.0, 0.0);
+                const Nbr<T> gq = gather<T, R>(H.idx, H.istride, n, r, ch.qcur);
+                V2 qz = mk<T>(0, 0);
                 if (ch.qprev) qz = ch.qprev[w];
-                qr = hop(c, gq.a.x, gq.b.x, gq.c.x, e, gq.x.x, qz.x, ONSITE);
-                qi = hop(c, gq.a.y, gq.b.y, gq.c.y, e, gq.x.y, qz.y, ONSITE);
+                qr = hop<T>(c, gq.a.x, gq.b.x, gq.c.x, e, gq.x.x, qz.x, ONSITE);
+                qi = hop<T>(c, gq.a.y, gq.b.y, gq.c.y, e, gq.x.y, qz.y, ONSITE);
                 qr = fma(d0, gs.a.x, fma(d1, gs.b.x, fma(d2, gs.c.x, qr)));
                 qi = fma(d0, gs.a.y, fma(d1, gs.b.y, fma(d2, gs.c.y, qi)));
             }
-            ch.qnxt[w] = make_double2(qr, qi);
+            ch.qnxt[w] = mk<T>(qr, qi);
             if (q_into_0) {
-                add_term(q_add, ODD, cr, ci, qr, qi);
+                add_term<T>(q_add, ODD, cr, ci, qr, qi);
             } else {
-                double2 a = FIRST ? make_double2(0.0, 0.0) : ch.qacc[w];
-                add_term(a, ODD, cr, ci, qr, qi);
+                V2 a = FIRST ? mk<T>(0, 0) : ch.qacc[w];
+                add_term<T>(a, ODD, cr, ci, qr, qi);
                 ch.qacc[w] = a;
             }
         }
@@ -319,34 +374,46 @@ __global__ void __launch_bounds__(kThreads) evolve_kernel(DevH H, double j0, dou
 // --------------------------------------------------------------------------------
 // out = H~ in, [X,H~] in, or V in = -(i E_max/hbar) [X,H~] in (Eq. 15).
 // --------------------------------------------------------------------------------
-template <int R, int OP, bool ONSITE, bool YPAR>
-__global__ void __launch_bounds__(kThreads) apply_kernel(DevH H, double scale,
-                                                         const double2* __restrict__ in,
-                                                         double2* __restrict__ out) {
+template <typename T, int R, int OP, bool ONSITE, bool YPAR>
+__global__ void __launch_bounds__(kThreads) apply_kernel(DevH H, double scaled,
+                                                         const vec2_t<T>* __restrict__ in,
+                                                         vec2_t<T>* __restrict__ out) {
     const int64_t n_items = H.n * R;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     const int r = threadIdx.x & (R - 1);
+    const T scale = (T)scaled;
     for (int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x; w < n_items; w += stride) {
         const int64_t n = w / R;
-        const Nbr g = gather<R>(H.idx, H.istride, n, r, in);
+        const Nbr<T> g = gather<T, R>(H.idx, H.istride, n, r, in);
         if constexpr (OP == 0) {
-            double e = 0.0;
-            if constexpr (ONSITE) e = __ldg(H.onsite + n);
-            out[w] = make_double2(hop(H.h, g.a.x, g.b.x, g.c.x, e, g.x.x, 0.0, ONSITE),
-                                  hop(H.h, g.a.y, g.b.y, g.c.y, e, g.x.y, 0.0, ONSITE));
+            T e = 0;
+            if constexpr (ONSITE) e = (T)__ldg(H.onsite + n);
+            const T h = (T)H.h;
+            out[w] = mk<T>(hop<T>(h, g.a.x, g.b.x, g.c.x, e, g.x.x, 0, ONSITE),
+                           hop<T>(h, g.a.y, g.b.y, g.c.y, e, g.x.y, 0, ONSITE));
         } else {
-            double d0, d1, d2;
+            double d0d, d1d, d2d;
             if constexpr (YPAR) {
                 const int p = __ldg(H.parity + n);
-                d0 = H.dh[p][0]; d1 = H.dh[p][1]; d2 = H.dh[p][2];
+                d0d = H.dh[p][0]; d1d = H.dh[p][1]; d2d = H.dh[p][2];
             } else {
-                d0 = H.dh[0][0]; d1 = H.dh[0][1]; d2 = H.dh[0][2];
+                d0d = H.dh[0][0]; d1d = H.dh[0][1]; d2d = H.dh[0][2];
             }
-            const double qr = fma(d0, g.a.x, fma(d1, g.b.x, d2 * g.c.x));
-            const double qi = fma(d0, g.a.y, fma(d1, g.b.y, d2 * g.c.y));
-            if constexpr (OP == 1) out[w] = make_double2(qr, qi);
-            else out[w] = make_double2(scale * qi, -scale * qr);   // -(i s)(qr + i qi)
+            const T d0 = (T)d0d, d1 = (T)d1d, d2 = (T)d2d;
+            const T qr = fma(d0, g.a.x, fma(d1, g.b.x, d2 * g.c.x));
+            const T qi = fma(d0, g.a.y, fma(d1, g.b.y, d2 * g.c.y));
+            if constexpr (OP == 1) out[w] = mk<T>(qr, qi);
+            else out[w] = mk<T>(scale * qi, -scale * qr);   // -(i s)(qr + i qi)
         }
+    }
+}
+
+// complex128 -> complex64 (rounded to nearest), n_items elements.
+__global__ void to_c64_kernel(const double2* __restrict__ in, float2* __restrict__ out, int64_t n_items) {
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x; w < n_items; w += stride) {
+        const double2 v = in[w];
+        out[w] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
     }
 }
 
@@ -412,38 +479,46 @@ static int one_wave_grid(K kernel, int64_t n_items) {
     if (b_) { constexpr bool NAME = true; __VA_ARGS__; } \
     else { constexpr bool NAME = false; __VA_ARGS__; }
 
-cudaError_t launch_kpm_sym(const DevH& H, int R, bool first, const double2* cur, const double2* prev,
-                           double2* out, double* partial, int grid, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_kpm_sym(const DevH& H, int R, bool first, const vec2_t<T>* cur, const vec2_t<T>* prev,
+                           vec2_t<T>* out, double* partial, int grid, cudaStream_t s) {
     const bool ons = H.onsite != nullptr;
     KG_DISPATCH_R(R, KG_BOOL(ons, ON, KG_BOOL(first, FI,
-        kpm_sym_kernel<RR, ON, FI><<<grid, kThreads, 0, s>>>(H, cur, prev, out, partial))));
+        kpm_sym_kernel<T, RR, ON, FI><<<grid, kThreads, 0, s>>>(H, cur, prev, out, partial))));
     return cudaGetLastError();
 }
 
-cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const double2* L, const double2* cur,
-                           const double2* prev, double2* out, double* partial, int grid,
+template <typename T>
+cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const vec2_t<T>* L, const vec2_t<T>* cur,
+                           const vec2_t<T>* prev, vec2_t<T>* out, double* partial, int grid,
                            cudaStream_t s) {
     const bool ons = H.onsite != nullptr;
     KG_DISPATCH_R(R, KG_BOOL(ons, ON, KG_BOOL(first, FI,
-        kpm_gen_kernel<RR, ON, FI><<<grid, kThreads, 0, s>>>(H, L, cur, prev, out, partial))));
+        kpm_gen_kernel<T, RR, ON, FI><<<grid, kThreads, 0, s>>>(H, L, cur, prev, out, partial))));
     return cudaGetLastError();
 }
 
+template <typename T>
 int kpm_grid(const DevH& H, int R, bool sym) {
     const bool ons = H.onsite != nullptr;
     const int64_t items = H.n * R;
-    int g = 1;
+    int g = stream_grid(items);
     auto pick = [&](auto k) { g = one_wave_grid(k, items); };
     switch (R) {
-#define KG_KPM_GRID_CASE(RV)                                                                  \
-        case RV:                                                                             \
-            if (sym) { if (ons) pick(kpm_sym_kernel<RV, true, false>); else pick(kpm_sym_kernel<RV, false, false>); } \
-            else { if (ons) pick(kpm_gen_kernel<RV, true, false>); else pick(kpm_gen_kernel<RV, false, false>); }     \
+#define KG_KPM_GRID_CASE(RV)                                                                   \
+        case RV:                                                                              \
+            if (sym) {                                                                        \
+                if (ons) pick(kpm_sym_kernel<T, RV, true, false>);                            \
+                else pick(kpm_sym_kernel<T, RV, false, false>);                               \
+            } else {                                                                          \
+                if (ons) pick(kpm_gen_kernel<T, RV, true, false>);                            \
+                else pick(kpm_gen_kernel<T, RV, false, false>);                               \
+            }                                                                                 \
             break;
         KG_KPM_GRID_CASE(1) KG_KPM_GRID_CASE(2) KG_KPM_GRID_CASE(4) KG_KPM_GRID_CASE(8)
         KG_KPM_GRID_CASE(16) KG_KPM_GRID_CASE(32) KG_KPM_GRID_CASE(64)
 #undef KG_KPM_GRID_CASE
-        default: g = stream_grid(items);
+        default: break;
     }
     return g;
 }
@@ -463,37 +538,60 @@ cudaError_t launch_reduce_ring(const double* ring, int slab0, int nslab, int rin
     return cudaGetLastError();
 }
 
-template <int R, int NCH, bool XC>
+template <typename T, int R, int NCH, bool XC>
 static void evolve_dispatch(const DevH& H, bool first, double j0, double cr, double ci,
-                            const Chains& ch, int /*grid*/, cudaStream_t s) {
+                            const ChainsT<T>& ch, cudaStream_t s) {
     const bool ons = H.onsite != nullptr, ypar = H.ytransport;
     const bool odd = first || cr == 0.0;   // the first step is the m = 1 term
     KG_BOOL(first, FI, KG_BOOL(ons, ON, KG_BOOL(ypar, YP, KG_BOOL(odd, OD,
         if constexpr (!FI || OD) {
-            const int g = one_wave_grid(evolve_kernel<R, NCH, XC, FI, ON, YP, OD>, H.n * R);
-            evolve_kernel<R, NCH, XC, FI, ON, YP, OD><<<g, kThreads, 0, s>>>(H, j0, cr, ci, ch);
+            const int g = one_wave_grid(evolve_kernel<T, R, NCH, XC, FI, ON, YP, OD>, H.n * R);
+            evolve_kernel<T, R, NCH, XC, FI, ON, YP, OD><<<g, kThreads, 0, s>>>(H, j0, cr, ci, ch);
         }))));
 }
 
+template <typename T>
 cudaError_t launch_evolve(const DevH& H, int R, int nch, bool xc, bool first, double j0, double cr,
-                          double ci, const Chains& ch, int grid, cudaStream_t s) {
+                          double ci, const ChainsT<T>& ch, cudaStream_t s) {
     if (nch < 1 || nch > 2) return cudaErrorInvalidValue;
     KG_DISPATCH_R(R,
-        if (nch == 1 && !xc) evolve_dispatch<RR, 1, false>(H, first, j0, cr, ci, ch, grid, s);
-        else if (nch == 1) evolve_dispatch<RR, 1, true>(H, first, j0, cr, ci, ch, grid, s);
-        else if (!xc) evolve_dispatch<RR, 2, false>(H, first, j0, cr, ci, ch, grid, s);
-        else evolve_dispatch<RR, 2, true>(H, first, j0, cr, ci, ch, grid, s));
+        if (nch == 1 && !xc) evolve_dispatch<T, RR, 1, false>(H, first, j0, cr, ci, ch, s);
+        else if (nch == 1) evolve_dispatch<T, RR, 1, true>(H, first, j0, cr, ci, ch, s);
+        else if (!xc) evolve_dispatch<T, RR, 2, false>(H, first, j0, cr, ci, ch, s);
+        else evolve_dispatch<T, RR, 2, true>(H, first, j0, cr, ci, ch, s));
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply(const DevH& H, int R, int op, double scale, const double2* in,
-                         double2* out, int grid, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_apply(const DevH& H, int R, int op, double scale, const vec2_t<T>* in,
+                         vec2_t<T>* out, cudaStream_t s) {
     const bool ons = H.onsite != nullptr, ypar = H.ytransport;
+    const int grid = stream_grid(H.n * R);
     KG_DISPATCH_R(R, KG_BOOL(ons, ON, KG_BOOL(ypar, YP,
-        if (op == 0) apply_kernel<RR, 0, ON, YP><<<grid, kThreads, 0, s>>>(H, scale, in, out);
-        else if (op == 1) apply_kernel<RR, 1, ON, YP><<<grid, kThreads, 0, s>>>(H, scale, in, out);
-        else apply_kernel<RR, 2, ON, YP><<<grid, kThreads, 0, s>>>(H, scale, in, out))));
+        if (op == 0) apply_kernel<T, RR, 0, ON, YP><<<grid, kThreads, 0, s>>>(H, scale, in, out);
+        else if (op == 1) apply_kernel<T, RR, 1, ON, YP><<<grid, kThreads, 0, s>>>(H, scale, in, out);
+        else apply_kernel<T, RR, 2, ON, YP><<<grid, kThreads, 0, s>>>(H, scale, in, out))));
     return cudaGetLastError();
 }
+
+cudaError_t launch_to_c64(const double2* in, float2* out, int64_t n_items, cudaStream_t s) {
+    to_c64_kernel<<<stream_grid(n_items), kThreads, 0, s>>>(in, out, n_items);
+    return cudaGetLastError();
+}
+
+#define KG_INSTANTIATE(T)                                                                          \
+    template cudaError_t launch_kpm_sym<T>(const DevH&, int, bool, const vec2_t<T>*,               \
+                                           const vec2_t<T>*, vec2_t<T>*, double*, int, cudaStream_t); \
+    template cudaError_t launch_kpm_gen<T>(const DevH&, int, bool, const vec2_t<T>*,               \
+                                           const vec2_t<T>*, const vec2_t<T>*, vec2_t<T>*, double*,   \
+                                           int, cudaStream_t);                                      \
+    template int kpm_grid<T>(const DevH&, int, bool);                                              \
+    template cudaError_t launch_evolve<T>(const DevH&, int, int, bool, bool, double, double, double, \
+                                          const ChainsT<T>&, cudaStream_t);                        \
+    template cudaError_t launch_apply<T>(const DevH&, int, int, double, const vec2_t<T>*,           \
+                                         vec2_t<T>*, cudaStream_t);
+
+KG_INSTANTIATE(double)
+KG_INSTANTIATE(float)
 
 }  // namespace kg

@@ -114,7 +114,7 @@ extern "C" kg_status kg_dos_moments_noalloc(const int32_t* idx_dev, const double
     KG_CUDA_TRY(cudaMemcpyAsync(phi0, phi_dev, (size_t)n * row, cudaMemcpyDeviceToDevice, s));
 
     double2* mu = (double2*)mu_dev;
-    KG_CUDA_TRY(launch_kpm_sym(H, R, true, phi0, nullptr, b1, first, grid, s));
+    KG_CUDA_TRY(launch_kpm_sym<double>(H, R, true, phi0, nullptr, b1, first, grid, s));
     KG_CUDA_TRY(launch_reduce_first(first, grid, R, true, mu, M, M, s));
     const int steps = (M - 1) / 2;
     const double2* cur = b1;
@@ -123,7 +123,7 @@ extern "C" kg_status kg_dos_moments_noalloc(const int32_t* idx_dev, const double
     int pending = 0, first_pending = 1;
     for (int k = 1; k <= steps; k++) {
         double* slab = ring + (int64_t)((k - 1) % kNoallocRing) * grid * R * 2;
-        KG_CUDA_TRY(launch_kpm_sym(H, R, false, cur, prev, out, slab, grid, s));
+        KG_CUDA_TRY(launch_kpm_sym<double>(H, R, false, cur, prev, out, slab, grid, s));
         if (++pending == kNoallocRing || k == steps) {
             KG_CUDA_TRY(launch_reduce_ring(ring, (first_pending - 1) % kNoallocRing, pending, kNoallocRing,
                                            grid, R, true, first_pending, mu, M, M, s));
