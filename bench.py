@@ -270,6 +270,27 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
 
+    # sigma^E1(E, t) on 201 energies from the timed moments (host sums, Eqs. 9 and 31)
+    def sigma_e1(mu):
+        en = np.linspace(-3 * w.gamma0_ev, 3 * w.gamma0_ev, 201)
+        mean = mu.mean(axis=0).real
+        dens = kg.kpm_sum(mean, en, h.emax_ev, h.area_nm2)
+        return kg.conductivity(kg.KG_SIGMA_E1, dens, DT * kg.HBAR_EV_FS / w.gamma0_ev)
+
+    t0 = time.perf_counter()
+    sig = sigma_e1(out.cpu().numpy())
+    sums_s = time.perf_counter() - t0
+    sigma = {"formula": "E1 (Eq. 9)", "energies": 201, "times": K + 1,
+             "time_s": ms * 1e-3 + sums_s, "host_sums_s": sums_s}
+    if PREC != "f64":
+        out64 = torch.zeros((R, K + 1, M), dtype=torch.complex128, device="cuda")
+        t0 = time.perf_counter()
+        kg.msd(h, phi_dev, M, K + 1, DT, bessel_tol=TOL, out=out64, precision=kg.KG_FP64)
+        f64_s = time.perf_counter() - t0
+        sig64 = sigma_e1(out64.cpu().numpy())
+        sigma["rel_err_vs_fp64_gpu"] = float(np.max(np.abs(sig - sig64)) / np.max(np.abs(sig64)))
+        sigma["fp64_gpu_time_s"] = f64_s + sums_s
+
     # sanity: the moments are finite and bounded by C_0 (|T_n| <= 1)
     c = out[:, 1:].real
     ok = bool(torch.isfinite(c).all()) and bool((c.abs() <= c[..., :1] * (1 + 1e-9) + 1e-300).all())
@@ -322,6 +343,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(phi_host.numel() * 16 / K),
                 "d2h_bytes_per_step": int(out_host.numel() * 16 / K), "seconds": e2e_s},
         "sanity_bounded_moments": ok,
+        "sigma": sigma,
     }
     if world == 1 and not args.no_cpu_baseline and CONFIG_NAME == DEFAULT_WORKLOAD:
         line["cpu_baseline"] = cpu_baseline()

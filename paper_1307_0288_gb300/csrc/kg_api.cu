@@ -338,8 +338,8 @@ static kg_status clear_zero_rows(kg_hamiltonian* h, int R, int count) {
 template <typename T>
 static kg_status dos_impl(kg_hamiltonian* h, int R, int M, const double* phi) {
     KG_TRY(ensure_vectors(h, R, 4));
-    KG_TRY(clear_zero_rows<T>(h, R, 4));
     KG_TRY(stage_input<T>(h, phi, R, 0, 3));
+    KG_TRY(clear_zero_rows<T>(h, R, 4));   // after staging: it writes complex128 rows into block 3
     return kpm_moments<T>(h, R, M, true, VT<T>(h, 0), VT<T>(h, 0), VT<T>(h, 1), VT<T>(h, 2),
                           (double2*)h->moments.p, M);
 }
@@ -349,10 +349,10 @@ static kg_status vac_impl(kg_hamiltonian* h, int R, int M, int NC, const Series&
     using V2 = vec2_t<T>;
     // blocks: 0 A, 1 B, 2 A', 3 B', 4 L, 5 p1(A), 6 p1(B), 7 kpm b0, 8 kpm b1
     KG_TRY(ensure_vectors(h, R, 9));
-    KG_TRY(clear_zero_rows<T>(h, R, 9));
     V2 *A = VT<T>(h, 0), *B = VT<T>(h, 1), *A2 = VT<T>(h, 2), *B2 = VT<T>(h, 3), *L = VT<T>(h, 4);
     const double vscale = h->emax / kHbarEvFs;
     KG_TRY(stage_input<T>(h, phi, R, 0, 7));
+    KG_TRY(clear_zero_rows<T>(h, R, 9));   // after staging: it writes complex128 rows into block 7
     KG_CUDA_TRY(launch_apply<T>(h->dev, R, 2, vscale, A, B, h->stream));   // B = V phi
     h->counters.other_launches += 1;
     double2* mu = (double2*)h->moments.p;
@@ -379,9 +379,9 @@ static kg_status msd_impl(kg_hamiltonian* h, int R, int M, int NC, const Series&
     using V2 = vec2_t<T>;
     // blocks: 0 psi, 1 xi, 2 psi', 3 xi', 4 p1(xi), 5 p1(psi), 6 q1, 7 q0
     KG_TRY(ensure_vectors(h, R, 8));
-    KG_TRY(clear_zero_rows<T>(h, R, 8));
     V2 *psi = VT<T>(h, 0), *xi = VT<T>(h, 1), *psi2 = VT<T>(h, 2), *xi2 = VT<T>(h, 3);
     KG_TRY(stage_input<T>(h, phi, R, 0, 7));
+    KG_TRY(clear_zero_rows<T>(h, R, 8));   // after staging: it writes complex128 rows into block 7
     KG_CUDA_TRY(cudaMemsetAsync(xi, 0, vec_bytes(h, R), h->stream));   // [X, U(0)] = 0
     double2* mu = (double2*)h->moments.p;
     KG_CUDA_TRY(cudaMemsetAsync(mu, 0, (size_t)R * NC * M * sizeof(double2), h->stream));
