@@ -42,6 +42,7 @@ WORKLOADS = {
     "msd-sheet-4096x2048-vac1pct-R8-M6000-dt2-c64": ((2048, 1024), 0.01, 8, 6000, 2.0, "c64"),
 }
 DEFAULT_WORKLOAD = "msd-sheet-2048x1024-vac0.5pct-R4-M3000-dt2"
+BATCHED_WORKLOAD = "dos-zgnr16-uneven-anderson-R64-M2000-batched"
 CELLS, VAC, R, M, DT, PREC = WORKLOADS[DEFAULT_WORKLOAD]
 METRIC = "Chebyshev site-updates/s and HBM GB/s vs peak; σ(E,t) time at 1e-5 err vs FP64"
 UNIT = "site-updates/s"
@@ -352,6 +353,92 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """16 uneven zigzag ribbons (widths 8..64 chains, lengths 1k..16k cells, Anderson
+    W = 0.5..2 eV), 64 vectors each, M = 2000 DOS moments, all in one persistent,
+    graph-captured launch.  One step = one kg_batched_dos_moments call."""
+    import torch
+    import paper_1307_0288_gb300 as kg
+
+    rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    rv, mm = 64, 2000
+    ws = ki.ribbon_set_16(n_vec=rv)
+    for w in ws:
+        w.vector_seed = 1000 + rv * rank
+    hs = [kg.from_workload(w) for w in ws]
+    phis = [torch.from_numpy(w.vectors(rv)).to("cuda") for w in ws]
+    n_sites = sum(w.n_sites for w in ws)
+    out = torch.zeros((len(ws), rv, mm), dtype=torch.complex128, device="cuda")
+    for _ in range(args.warmup):
+        kg.batched_dos_moments(hs, phis, mm, out=out)
+    tune = kg.batched_tuning()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    e0.record()
+    for _ in range(args.steps):
+        kg.batched_dos_moments(hs, phis, mm, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # end to end from pinned host inputs to host moments
+    phis_h = [p.cpu().pin_memory() for p in phis]
+    out_h = torch.zeros((len(ws), rv, mm), dtype=torch.complex128).pin_memory()
+    t0 = time.perf_counter()
+    kg.batched_dos_moments(hs, phis_h, mm, out=out_h)
+    e2e_s = time.perf_counter() - t0
+    work = float(n_sites) * rv * (mm - 1) * args.steps * world
+    steps_per_call = (mm + 1) // 2
+    step_ms = ms / args.steps / steps_per_call
+    flops = KPM_FLOPS_PER_SITE_STEP * n_sites * rv
+    achieved = flops / (step_ms * 1e-3) / 1e12
+    bytes_step = n_sites * (12 + 48 * rv)
+    peaks = _peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    c = out.real
+    ok = bool(torch.isfinite(c).all()) and bool((c.abs() <= c[..., :1] * (1 + 1e-9)).all())
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": work / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": BATCHED_WORKLOAD, "instances": len(ws), "sites": n_sites,
+                   "vectors_per_instance": rv, "moments": mm,
+                   "l2": "inputs larger than L2 (2 x 6.9 GB vector blocks)",
+                   "parallelism": f"replicas x{world} (independent random vectors)"},
+        "roofline": {"bound": "alu", "kernel": "batched_kpm_kernel<64,RB> (persistent FP64 doubling KPM)",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "avg_step_ms": step_ms,
+                     "hbm": {"achieved_gbs": bytes_step / (step_ms * 1e-3) / 1e9, "peak_gbs": hbm_peak}},
+        "autotune": tune,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "e2e": {"value": float(n_sites) * rv * (mm - 1) / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(p.numel() for p in phis_h) * 16),
+                "d2h_bytes_per_step": int(out_h.numel() * 16), "seconds": e2e_s},
+        "sanity_bounded_moments": ok,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -359,9 +446,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCHED_WORKLOAD], default=DEFAULT_WORKLOAD)
     args = ap.parse_args()
     global CELLS, VAC, R, M, DT, PREC, CONFIG_NAME
+    if args.workload == BATCHED_WORKLOAD:
+        return run_batched(args)
     CELLS, VAC, R, M, DT, PREC = WORKLOADS[args.workload]
     CONFIG_NAME = args.workload
     if args.warmup < 1 or args.steps < 1:

@@ -160,6 +160,39 @@ kg_status kg_apply(kg_hamiltonian* h, int op, const double* in_dev, double* out_
 kg_status kg_evolve(kg_hamiltonian* h, double dt, int which, double bessel_tol,
                     const double* in_dev, double* out_dev, int n_vectors);
 
+/* ------------------------------------------------------------------------- */
+/* Batched instances in one persistent launch                                */
+/* ------------------------------------------------------------------------- */
+
+/* DOS moments (Eq. 32, Algorithm 5) of n_h independent Hamiltonians at once, e.g. many
+ * ribbons of different widths, lengths and disorder, R random vectors each.  All members
+ * must live on the current device and use transport along x (sheet or ZGNR).  The
+ * members are concatenated into one block-diagonal table; one persistent kernel runs
+ * every Chebyshev step of every member, each CTA waiting (bounded) only for the CTAs
+ * that hold its sites' neighbours; the call's device work is captured once in a CUDA
+ * graph and replayed.  The block width (vectors per thread group: 8..64) is chosen by a
+ * measured autotuner on the first call for a given member set and R.
+ *   hs       n_h member handles (the batch is cached for the same list and R).
+ *   run      n_moments M, n_vectors R (power of two <= 64), precision KG_FP64.
+ *   phis     n_h pointers, host or device, member i's vectors [N_i][R][2].
+ *   mu_out   host or device [n_h][R][M][2].
+ * KG_ETIMEOUT if a CTA's wait for its neighbours gave up (the context stays usable). */
+kg_status kg_batched_dos_moments(kg_hamiltonian* const* hs, int n_h, const kg_run* run,
+                                 const double* const* phis, double* mu_out);
+
+/* Result of the autotuner for the cached batch: chosen block width, its time per
+ * recursion step (ms), the CTA count, and up to max_log measured (width, ms) pairs. */
+kg_status kg_batched_tuning(int* block_width, double* ms_per_step, int* n_ctas, int max_log,
+                            int* log_width, double* log_ms);
+
+/* Frees the cached batch (its device memory and graphs). */
+kg_status kg_batched_release(void);
+
+/* Test hook for failure detection: CTA `cta` of the cached batch stops publishing its
+ * step flags after step 0, so its neighbours' bounded waits run out and the next
+ * kg_batched_dos_moments returns KG_ETIMEOUT.  -1 turns the hook off. */
+kg_status kg_batched_test_stall(int cta);
+
 /* DOS moments without device memory allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that cannot call

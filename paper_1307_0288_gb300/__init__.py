@@ -77,6 +77,10 @@ ABI = [
     ("kg_kpm_sum", _I, [_P, _I, _I, _P, _I, _D, _D, _P]),
     ("kg_conductivity", _I, [_I, _P, _I, _I, _D, _P]),
     ("kg_dos_moments_noalloc", _I, [_P, _P, _I64, _D, _I, _I, _P, _P, _P]),
+    ("kg_batched_dos_moments", _I, [_P, _I, ctypes.POINTER(_Run), _P, _P]),
+    ("kg_batched_tuning", _I, [_P, _P, _P, _I, _P, _P]),
+    ("kg_batched_release", _I, []),
+    ("kg_batched_test_stall", _I, [_I]),
 ]
 
 _lib = None
@@ -297,6 +301,50 @@ def dos_moments_noalloc(idx_dev, onsite_dev, n_sites: int, hopping: float, phi_d
         int(n_sites), float(hopping), r, m, ctypes.c_void_p(phi_dev.data_ptr()),
         ctypes.c_void_p(mu_dev.data_ptr()), ctypes.c_void_p(s)))
     return mu_dev
+
+
+def batched_dos_moments(hs, phis, n_moments: int, out=None):
+    """kg_batched_dos_moments -> complex [n_h][R][M].  hs: list of Hamiltonian;
+    phis: list of [N_i][R] complex128 (numpy or torch CUDA), same R for all."""
+    n_h = len(hs)
+    r = _nvec(phis[0], hs[0].n)
+    keep = []
+    ptrs = (ctypes.c_void_p * n_h)()
+    for i, (h, p) in enumerate(zip(hs, phis)):
+        if _nvec(p, h.n) != r:
+            raise ValueError("all members need the same number of vectors")
+        addr, k = _complex_in(p)
+        keep.append(k)
+        ptrs[i] = addr
+    handles = (ctypes.c_void_p * n_h)(*[h.handle.value for h in hs])
+    if out is None:
+        res = np.zeros((n_h, r, n_moments), dtype=np.complex128)
+        op = res.ctypes.data
+    else:
+        res = out
+        op = out.data_ptr()
+    run = _run(n_moments, r, 1, KG_FP64)
+    _check(lib().kg_batched_dos_moments(handles, n_h, ctypes.byref(run), ptrs, ctypes.c_void_p(op)))
+    return res
+
+
+def batched_tuning() -> dict:
+    """kg_batched_tuning: the autotuner's choice and its measurements."""
+    bw, nc = ctypes.c_int(), ctypes.c_int()
+    ms = ctypes.c_double()
+    lw = (ctypes.c_int * 8)()
+    lm = (ctypes.c_double * 8)()
+    _check(lib().kg_batched_tuning(ctypes.byref(bw), ctypes.byref(ms), ctypes.byref(nc), 8, lw, lm))
+    log = [(lw[k], lm[k]) for k in range(8) if lw[k]]
+    return {"block_width": bw.value, "ms_per_step": ms.value, "n_ctas": nc.value, "log": log}
+
+
+def batched_release():
+    _check(lib().kg_batched_release())
+
+
+def batched_test_stall(cta: int):
+    _check(lib().kg_batched_test_stall(int(cta)))
 
 
 def timing_enable(h: Hamiltonian, enable: bool = True):

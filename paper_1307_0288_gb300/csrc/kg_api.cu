@@ -65,6 +65,9 @@ struct kg_hamiltonian {
 
 namespace kg {
 
+const DevH& hamiltonian_dev(const kg_hamiltonian* h) { return h->dev; }
+cudaStream_t hamiltonian_stream(const kg_hamiltonian* h) { return h->stream; }
+
 static constexpr int kRing = 256;   // partial-sum slabs reduced per launch
 
 static kg_status check_device(kg_hamiltonian* h) {

@@ -71,8 +71,12 @@ struct DevH {
     bool ytransport = false;
 };
 
-// Number of co-resident 256-thread CTAs per SM for a kernel, and the SM count.
+// Number of SMs of the current device.
 int sm_count();
+
+// Device description of a built Hamiltonian (defined with the handle in kg_api.cu).
+const DevH& hamiltonian_dev(const kg_hamiltonian* h);
+cudaStream_t hamiltonian_stream(const kg_hamiltonian* h);
 
 // Complex vector element of each precision.
 template <typename T>
