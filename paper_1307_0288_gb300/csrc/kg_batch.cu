@@ -309,8 +309,9 @@ static kg_status member_table(const kg_hamiltonian* h, std::vector<int32_t>* out
 }
 
 static kg_status build_schedule(Batch* b, int rb, Batch::Sched* s) {
-    int per_sm = 1;
+    int per_sm = 0;
     KG_BATCH_DISPATCH(b->R, rb, per_sm = batched_occupancy<R, RB>(b->onsite));
+    if (per_sm < 1) return fail(KG_EINVAL, "batched: no kernel for this (R, block width)");
     const int n_inst = (int)b->members.size();
     const int64_t wave = (int64_t)sm_count() * per_sm;
     int64_t budget = std::max<int64_t>(wave, n_inst);
@@ -419,7 +420,7 @@ static kg_status create_batch(kg_hamiltonian* const* hs, int n_h, int R, std::un
     b->n_total = total;
     const size_t b_idx = ((size_t)3 * total * sizeof(int32_t) + 255) & ~(size_t)255;
     const size_t b_on = b->onsite ? (((size_t)(total + 1) * sizeof(double) + 255) & ~(size_t)255) : 0;
-    const size_t b_hop = 256 + (size_t)n_h * sizeof(double);
+    const size_t b_hop = ((size_t)n_h * sizeof(double) + 255) & ~(size_t)255;
     const size_t b_vec = (((size_t)(total + 1) * R * sizeof(double2)) + 255) & ~(size_t)255;
     const size_t b_flags = 256 + (size_t)sm_count() * 64 * sizeof(int);
     const size_t bytes = b_idx + b_on + b_hop + 2 * b_vec + b_flags;
@@ -435,6 +436,9 @@ static kg_status create_batch(kg_hamiltonian* const* hs, int n_h, int R, std::un
     b->B = (double2*)p; p += b_vec;
     b->error = (int*)p;
     b->flags = (int*)p + 64;
+    // every double2 block must sit on a 16-byte boundary
+    for (const void* q : {(const void*)b->A, (const void*)b->B, (const void*)b->hop, (const void*)b->idx})
+        if ((uintptr_t)q % 16 != 0) return fail(KG_EINVAL, "batched: internal layout misaligned");
     KG_CUDA_TRY(cudaMemsetAsync(b->mem, 0, bytes, b->stream));
     std::vector<double> hop(n_h);
     for (int i = 0; i < n_h; i++) {
@@ -520,7 +524,7 @@ static kg_status run_graph(Batch* b, int rb, int M) {
         a.stall_cta = b->stall_cta;
         if (direct) {
             KG_CUDA_TRY(cudaMemsetAsync(b->error, 0, 64 * sizeof(int) + (size_t)s->n_cta * sizeof(int), b->stream));
-            cudaError_t e = cudaSuccess;
+            cudaError_t e = cudaErrorInvalidConfiguration;   // no instantiation for (R, RB)
             KG_BATCH_DISPATCH(b->R, rb, e = (launch_batched<R, RB>(a, b->onsite, b->stream)));
             KG_CUDA_TRY(e);
             batched_reduce_kernel<<<dim3(steps, (unsigned)b->members.size()), 64, 0, b->stream>>>(
@@ -531,7 +535,7 @@ static kg_status run_graph(Batch* b, int rb, int M) {
         cudaGraph_t g = nullptr;
         KG_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e1 = cudaMemsetAsync(b->error, 0, 64 * sizeof(int) + (size_t)s->n_cta * sizeof(int), b->stream);
-        cudaError_t e2 = cudaSuccess;
+        cudaError_t e2 = cudaErrorInvalidConfiguration;   // no instantiation for (R, RB)
         KG_BATCH_DISPATCH(b->R, rb, e2 = (launch_batched<R, RB>(a, b->onsite, b->stream)));
         batched_reduce_kernel<<<dim3(steps, (unsigned)b->members.size()), 64, 0, b->stream>>>(
             b->partial, s->inst_c0, s->inst_c1, s->n_cta, b->R, M, b->mu);
