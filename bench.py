@@ -220,7 +220,9 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    w = ki.sheet_cells(*CELLS, vacancy_conc=VAC, vector_seed=1000 + R * rank, n_vec=R)
+    from paper_1307_0288_gb300 import replicas
+    w = ki.sheet_cells(*CELLS, vacancy_conc=VAC, vector_seed=replicas.rank_vector_seed(1000, rank, R),
+                       n_vec=R)
     stream = torch.cuda.Stream()
     h = kg.from_workload(w, stream=stream)
     n_p = len(kg.bessel_series(h.emax_ev * DT / w.gamma0_ev, TOL))
@@ -368,8 +370,9 @@ def run_batched(args):
         dist.init_process_group("nccl")
     rv, mm = 64, 2000
     ws = ki.ribbon_set_16(n_vec=rv)
+    from paper_1307_0288_gb300 import replicas
     for w in ws:
-        w.vector_seed = 1000 + rv * rank
+        w.vector_seed = replicas.rank_vector_seed(1000, rank, rv)
     hs = [kg.from_workload(w) for w in ws]
     phis = [torch.from_numpy(w.vectors(rv)).to("cuda") for w in ws]
     n_sites = sum(w.n_sites for w in ws)

@@ -226,3 +226,27 @@ def test_invalid_runs_are_rejected():
         kg.vac(h, w.vectors(1), 10, 3, -1.0)
     with pytest.raises(kg.KgError):
         kg.dos_moments(h, w.vectors(1), 0)
+
+
+def test_sigma_pipeline_matches_oracle():
+    """sigma^GK (Eq. 6) from VAC moments and sigma^E1 / sigma^E2 (Eqs. 9, 11) from MSD
+    moments on the 201-point energy grid: GPU moments + library sums against oracle
+    moments + oracle sums (Eqs. 29-31, 35)."""
+    from oracle import post
+    w = ki.sheet_cells(32, 32, vacancy_conc=0.01)
+    h = kg.from_workload(w)
+    ho = oracle.from_workload(w)
+    phi = w.vectors(2)
+    en = post.energy_grid()
+    for fn, ofn, dt, formulas in [(kg.vac, oracle.vac_moments, 1.0, [(kg.KG_SIGMA_GK, post.sigma_gk)]),
+                                  (kg.msd, oracle.msd_moments, 2.0,
+                                   [(kg.KG_SIGMA_E1, post.sigma_e1), (kg.KG_SIGMA_E2, post.sigma_e2)])]:
+        mu = fn(h, phi, 512, 8, dt).mean(axis=0)
+        mu_o = np.mean([ofn(ho, phi[:, r], 512, 8, dt) for r in range(2)], axis=0)
+        dens = kg.kpm_sum(mu.real, en, h.emax_ev, h.area_nm2)
+        dens_o = post.kpm_density(mu_o, en, ho.emax_ev, ho.area_nm2)
+        t = post.time_grid(8, dt)
+        for f, of in formulas:
+            s = kg.conductivity(f, dens, t[1])
+            so = of(dens_o, t)
+            assert _rel(s, so) < TOL_MOMENTS, f
