@@ -193,6 +193,41 @@ kg_status kg_batched_release(void);
  * kg_batched_dos_moments returns KG_ETIMEOUT.  -1 turns the hook off. */
 kg_status kg_batched_test_stall(int cta);
 
+/* ------------------------------------------------------------------------- */
+/* Surrogate MLP for sigma(E, t) (not part of the paper)                      */
+/* ------------------------------------------------------------------------- */
+
+/* A small network trained on sigma(E, t) curves the method generates, used to predict
+ * ensemble-averaged sigma(E, t) across vacancy concentrations (the method itself stays
+ * the fallback and the judge of its error).  Architecture: 3 inputs -> 4 hidden layers
+ * of 256 GELU units -> 1 output; BF16 weights and activations at the matrix-multiply
+ * inputs with FP32 accumulation (the 256 x 256 layers on the tcgen05 tensor cores),
+ * FP32 master weights, Adam (beta1 0.9, beta2 0.999, eps 1e-8), loss = mean (y - t)^2.
+ * Flat FP32 parameter layout (KG_MLP_PARAMS values): W1 [256][3], b1 [256], then for
+ * layers 2..4 W [256][256] ([out][in]) and b [256], then W5 [256], b5 [1]. */
+#define KG_MLP_PARAMS 198657
+typedef struct kg_mlp kg_mlp;
+
+/* Uploads the initial parameters (host or device, caller-owned) to the current device;
+ * every later call is issued on cuda_stream. */
+kg_status kg_mlp_create(const float* params, void* cuda_stream, kg_mlp** out);
+void kg_mlp_destroy(kg_mlp* m);
+/* Current FP32 parameters into params (host or device [KG_MLP_PARAMS]). */
+kg_status kg_mlp_get_params(kg_mlp* m, float* params);
+/* Inference: y [n] for inputs x [n][3] (host or device). */
+kg_status kg_mlp_forward(kg_mlp* m, const float* x, int64_t n, float* y);
+/* Loss and FP32 gradient (host or device [KG_MLP_PARAMS], may be NULL) of one batch. */
+kg_status kg_mlp_gradients(kg_mlp* m, const float* x, const float* t, int64_t n, float* grad,
+                           double* loss);
+/* One Adam step on the batch (x [n][3], targets t [n]); loss before the step (may be NULL). */
+kg_status kg_mlp_train_step(kg_mlp* m, const float* x, const float* t, int64_t n, float lr,
+                            double* loss);
+/* Number of kernels this handle has launched. */
+kg_status kg_mlp_launches(kg_mlp* m, int64_t* launches);
+/* Test hook: D [rows][256] (FP32, device) = A [rows][k] * B [256][k]^T on the tensor cores,
+ * A and B BF16 device arrays, k a multiple of 64. */
+kg_status kg_mlp_gemm_test(const void* a_dev, const void* b_dev, int64_t rows, int k, float* d_dev);
+
 /* DOS moments without device memory allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that cannot call

@@ -81,6 +81,14 @@ ABI = [
     ("kg_batched_tuning", _I, [_P, _P, _P, _I, _P, _P]),
     ("kg_batched_release", _I, []),
     ("kg_batched_test_stall", _I, [_I]),
+    ("kg_mlp_create", _I, [_P, _P, ctypes.POINTER(_P)]),
+    ("kg_mlp_destroy", None, [_P]),
+    ("kg_mlp_get_params", _I, [_P, _P]),
+    ("kg_mlp_forward", _I, [_P, _P, _I64, _P]),
+    ("kg_mlp_gradients", _I, [_P, _P, _P, _I64, _P, ctypes.POINTER(_D)]),
+    ("kg_mlp_train_step", _I, [_P, _P, _P, _I64, ctypes.c_float, ctypes.POINTER(_D)]),
+    ("kg_mlp_launches", _I, [_P, ctypes.POINTER(_I64)]),
+    ("kg_mlp_gemm_test", _I, [_P, _P, _I64, _I, _P]),
 ]
 
 _lib = None
@@ -345,6 +353,91 @@ def batched_release():
 
 def batched_test_stall(cta: int):
     _check(lib().kg_batched_test_stall(int(cta)))
+
+
+KG_MLP_PARAMS = 198657
+
+
+def _f32(x):
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.float32:
+            raise ValueError("expected float32")
+        return _ptr(x)
+    return _ptr(np.ascontiguousarray(x, dtype=np.float32))
+
+
+class Mlp:
+    """Owns a ``kg_mlp*`` (surrogate network on the device)."""
+
+    def __init__(self, params, stream=None):
+        pp, keep = _f32(params)
+        if (keep.numel() if _is_torch(keep) else keep.size) != KG_MLP_PARAMS:
+            raise ValueError(f"expected {KG_MLP_PARAMS} parameters")
+        s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+        out = ctypes.c_void_p()
+        _check(lib().kg_mlp_create(ctypes.c_void_p(pp), ctypes.c_void_p(s), ctypes.byref(out)))
+        self._m = out
+
+    def close(self):
+        if self._m is not None and self._m.value:
+            lib().kg_mlp_destroy(self._m)
+        self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(KG_MLP_PARAMS, dtype=np.float32)
+        _check(lib().kg_mlp_get_params(self._m, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def forward(self, x, out=None):
+        """kg_mlp_forward: x [n][3] float32 -> y [n]."""
+        xp, kx = _f32(x)
+        n = int(x.shape[0])
+        if out is None:
+            res = np.zeros(n, dtype=np.float32)
+            op = res.ctypes.data
+        else:
+            res, op = out, _ptr(out, writable=True)[0]
+        _check(lib().kg_mlp_forward(self._m, ctypes.c_void_p(xp), n, ctypes.c_void_p(op)))
+        return res
+
+    def gradients(self, x, t):
+        """kg_mlp_gradients -> (loss, grad [KG_MLP_PARAMS])."""
+        xp, kx = _f32(x)
+        tp, kt = _f32(t)
+        g = np.zeros(KG_MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(lib().kg_mlp_gradients(self._m, ctypes.c_void_p(xp), ctypes.c_void_p(tp), int(x.shape[0]),
+                                      ctypes.c_void_p(g.ctypes.data), ctypes.byref(loss)))
+        return loss.value, g
+
+    def train_step(self, x, t, lr: float) -> float:
+        """kg_mlp_train_step (one Adam step) -> loss before the step."""
+        xp, kx = _f32(x)
+        tp, kt = _f32(t)
+        loss = ctypes.c_double()
+        _check(lib().kg_mlp_train_step(self._m, ctypes.c_void_p(xp), ctypes.c_void_p(tp), int(x.shape[0]),
+                                       float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def launches(self) -> int:
+        n = ctypes.c_int64()
+        _check(lib().kg_mlp_launches(self._m, ctypes.byref(n)))
+        return n.value
+
+
+def mlp_gemm_test(a_dev, b_dev, out_dev):
+    """kg_mlp_gemm_test: out [rows][256] fp32 = a [rows][k] bf16 @ b [256][k]^T (device tensors)."""
+    rows, k = int(a_dev.shape[0]), int(a_dev.shape[1])
+    _check(lib().kg_mlp_gemm_test(ctypes.c_void_p(a_dev.data_ptr()), ctypes.c_void_p(b_dev.data_ptr()),
+                                  rows, k, ctypes.c_void_p(out_dev.data_ptr())))
+    return out_dev
 
 
 def timing_enable(h: Hamiltonian, enable: bool = True):

@@ -1,0 +1,70 @@
+"""Surrogate MLP kernels: the tcgen05 BF16 GEMM against a plain PyTorch FP32 matmul of
+the same BF16 operands, and the network's forward pass and gradients against the FP64
+oracle MLP (BF16 tolerance), and Adam training."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1307_0288_gb300 as kg  # noqa: E402
+from oracle import mlp as omlp  # noqa: E402
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("rows,k", [(128, 64), (300, 256), (1, 256), (1000, 512)])
+def test_tcgen05_gemm_matches_fp32_matmul(rows, k):
+    g = torch.Generator().manual_seed(rows + k)
+    a = torch.randn(rows, k, generator=g).to(torch.bfloat16).cuda()
+    b = torch.randn(256, k, generator=g).to(torch.bfloat16).cuda()
+    d = torch.full((rows, 256), float("nan"), dtype=torch.float32, device="cuda")
+    kg.mlp_gemm_test(a, b, d)
+    ref = a.float() @ b.float().T
+    err = (d - ref).abs().max().item() / ref.abs().max().item()
+    assert err < 1e-5, err
+
+
+def _batch(n, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+    t = (np.sin(2 * x[:, 0]) + x[:, 1] * x[:, 2]).astype(np.float32)
+    return x, t
+
+
+def test_forward_matches_oracle():
+    p = omlp.init_params(7)
+    net = kg.Mlp(p.astype(np.float32))
+    x, _ = _batch(1000, 1)
+    y = net.forward(x)
+    ref = omlp.forward(p, x)
+    assert _rel(y, ref) < 3e-2
+
+
+def test_gradients_match_oracle():
+    """Per parameter block, |g_gpu - g_fp64| / |g_fp64| (2-norms) within BF16 tolerance."""
+    p = omlp.init_params(8)
+    net = kg.Mlp(p.astype(np.float32))
+    x, t = _batch(777, 2)
+    loss, g = net.gradients(x, t)
+    loss_o, g_o = omlp.gradients(p, x, t)
+    assert abs(loss - loss_o) / loss_o < 2e-2
+    k = 0
+    for name, shape in omlp.param_layout():
+        size = int(np.prod(shape))
+        a, b = g[k:k + size], g_o[k:k + size]
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 5e-2, name
+        k += size
+
+
+def test_adam_training_reduces_loss():
+    p = omlp.init_params(9)
+    net = kg.Mlp(p.astype(np.float32))
+    x, t = _batch(4096, 3)
+    first = net.train_step(x, t, 1e-3)
+    for _ in range(150):
+        last = net.train_step(x, t, 1e-3)
+    assert last < 0.1 * first, (first, last)
+    assert np.all(np.isfinite(net.params()))

@@ -445,3 +445,37 @@ def test_planted_mistakes_are_caught(mutation):
     with oracle.mutation(mutation):
         bad = _pin_errors()
     assert max(bad.values()) > 1e-6, bad
+
+
+# ------------------------------------------------------------------ surrogate MLP oracle
+
+def test_mlp_oracle_gradients_match_finite_differences():
+    """Reverse-mode gradients of the FP64 MLP equal central finite differences of the
+    loss (relative 1e-6) for sampled parameters of every layer."""
+    from oracle import mlp
+    hidden = 16                      # same code path, small enough for differences
+    flat = mlp.init_params(3, hidden) + 0.01
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=(37, 3))
+    t = rng.normal(size=37)
+    l0, g = mlp.gradients(flat, x, t, hidden)
+    assert abs(l0 - mlp.loss(flat, x, t, hidden)) < 1e-14
+    idx = np.concatenate([rng.choice(len(flat), 60, replace=False), [len(flat) - 1, 0]])
+    h = 1e-6
+    for k in idx:
+        e = np.zeros_like(flat)
+        e[k] = h
+        fd = (mlp.loss(flat + e, x, t, hidden) - mlp.loss(flat - e, x, t, hidden)) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(abs(fd), 1e-3), (k, fd, g[k])
+
+
+def test_mlp_oracle_gelu_and_layout():
+    """GELU closed forms (GELU(0) = 0, GELU(z) -> z for large z, GELU' = derivative)
+    and the parameter count 3*256 + 256 + 3*(256^2 + 256) + 256 + 1."""
+    from oracle import mlp
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0
+    assert abs(mlp.gelu(np.array([10.0]))[0] - 10.0) < 1e-12
+    z = np.linspace(-4, 4, 41)
+    fd = (mlp.gelu(z + 1e-6) - mlp.gelu(z - 1e-6)) / 2e-6
+    assert np.max(np.abs(fd - mlp.gelu_grad(z))) < 1e-8
+    assert mlp.n_params() == 3 * 256 + 256 + 3 * (256 * 256 + 256) + 256 + 1 == 198657
