@@ -43,6 +43,7 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "msd-sheet-2048x1024-vac0.5pct-R4-M3000-dt2"
 BATCHED_WORKLOAD = "dos-zgnr16-uneven-anderson-R64-M2000-batched"
+SURROGATE_WORKLOAD = "surrogate-mlp-3x256x4-bf16-batch1M"
 CELLS, VAC, R, M, DT, PREC = WORKLOADS[DEFAULT_WORKLOAD]
 METRIC = "Chebyshev site-updates/s and HBM GB/s vs peak; σ(E,t) time at 1e-5 err vs FP64"
 UNIT = "site-updates/s"
@@ -442,6 +443,81 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_surrogate(args):
+    """Surrogate MLP (3 -> 4 x 256 GELU -> 1, BF16 tensor-core kernels): batch-1M
+    inference, one step = one forward over 1,048,576 inputs; also the time of one Adam
+    training step on 65,536 samples."""
+    import torch
+    import paper_1307_0288_gb300 as kg
+    from oracle import mlp as om   # only for the parameter initialisation rule
+
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    n = 1 << 20
+    net = kg.Mlp(om.init_params(1).astype(np.float32))
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = (torch.rand((n, 3), generator=g, device="cuda") * 2 - 1).contiguous()
+    y = torch.zeros(n, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        net.forward(x, out=y)
+    net.timing_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record()
+    for _ in range(args.steps):
+        net.forward(x, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    tm = net.timing_read()
+    net.timing_enable(False)
+    flop_sample = 2 * (3 * 256 + 3 * 256 * 256 + 256)
+    # end to end: host inputs and outputs
+    xh = x.cpu().pin_memory()
+    yh = torch.zeros(n, dtype=torch.float32).pin_memory()
+    t0 = time.perf_counter()
+    net.forward(xh, out=yh)
+    e2e_s = time.perf_counter() - t0
+    # one training step (forward, backward, Adam) on 65,536 samples
+    xt = x[:65536].contiguous()
+    tt = torch.sin(2 * xt[:, 0]) + xt[:, 1] * xt[:, 2]
+    for _ in range(3):
+        net.train_step(xt, tt, 1e-4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(10):
+        net.train_step(xt, tt, 1e-4)
+    torch.cuda.synchronize()
+    train_s = (time.perf_counter() - t0) / 10
+    peaks = _peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    achieved = tm["gemm_flop"] / (tm["gemm_ms"] * 1e-3) / 1e12
+    line = {
+        "metric": "surrogate sigma(E,t) predictions/s", "value": n * args.steps / (ms * 1e-3),
+        "unit": "samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": SURROGATE_WORKLOAD, "batch": n, "hidden": [256] * 4,
+                   "l2": "activations 1M x 256 x 2 B = 512 MB per layer, larger than L2"},
+        "roofline": {"bound": "tensor", "kernel": "umma_gemm_kernel (tcgen05 BF16 128x256 tiles)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"
+                     if "bf16_tflops" in peaks else "fallback",
+                     "gemm_ms_per_step": tm["gemm_ms"] / args.steps,
+                     "gemm_share_of_step": tm["gemm_ms"] / ms},
+        "model_tflops": flop_sample * n * args.steps / (ms * 1e-3) / 1e12,
+        "train_step_ms_65536": train_s * 1e3,
+        "gpu_launches": int(tm["gemm_launches"] / 3 * 5),
+        "clocks": clk,
+        "e2e": {"value": n / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": n * 12,
+                "d2h_bytes_per_step": n * 4, "seconds": e2e_s},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -449,11 +525,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCHED_WORKLOAD], default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCHED_WORKLOAD, SURROGATE_WORKLOAD],
+                    default=DEFAULT_WORKLOAD)
     args = ap.parse_args()
     global CELLS, VAC, R, M, DT, PREC, CONFIG_NAME
     if args.workload == BATCHED_WORKLOAD:
         return run_batched(args)
+    if args.workload == SURROGATE_WORKLOAD:
+        return run_surrogate(args)
     CELLS, VAC, R, M, DT, PREC = WORKLOADS[args.workload]
     CONFIG_NAME = args.workload
     if args.warmup < 1 or args.steps < 1:

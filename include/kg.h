@@ -224,6 +224,10 @@ kg_status kg_mlp_train_step(kg_mlp* m, const float* x, const float* t, int64_t n
                             double* loss);
 /* Number of kernels this handle has launched. */
 kg_status kg_mlp_launches(kg_mlp* m, int64_t* launches);
+/* CUDA-event timing of the tensor-core GEMM launches: enable (1) / disable (0) and reset;
+ * read the summed GEMM time (ms), launch count and their 2MNK flops since the reset. */
+kg_status kg_mlp_timing_enable(kg_mlp* m, int enable);
+kg_status kg_mlp_timing_read(kg_mlp* m, double* gemm_ms, int64_t* gemm_launches, double* gemm_flop);
 /* Test hook: D [rows][256] (FP32, device) = A [rows][k] * B [256][k]^T on the tensor cores,
  * A and B BF16 device arrays, k a multiple of 64. */
 kg_status kg_mlp_gemm_test(const void* a_dev, const void* b_dev, int64_t rows, int k, float* d_dev);

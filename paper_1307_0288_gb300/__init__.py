@@ -88,6 +88,8 @@ ABI = [
     ("kg_mlp_gradients", _I, [_P, _P, _P, _I64, _P, ctypes.POINTER(_D)]),
     ("kg_mlp_train_step", _I, [_P, _P, _P, _I64, ctypes.c_float, ctypes.POINTER(_D)]),
     ("kg_mlp_launches", _I, [_P, ctypes.POINTER(_I64)]),
+    ("kg_mlp_timing_enable", _I, [_P, _I]),
+    ("kg_mlp_timing_read", _I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64), ctypes.POINTER(_D)]),
     ("kg_mlp_gemm_test", _I, [_P, _P, _I64, _I, _P]),
 ]
 
@@ -430,6 +432,14 @@ class Mlp:
         n = ctypes.c_int64()
         _check(lib().kg_mlp_launches(self._m, ctypes.byref(n)))
         return n.value
+
+    def timing_enable(self, enable: bool = True):
+        _check(lib().kg_mlp_timing_enable(self._m, 1 if enable else 0))
+
+    def timing_read(self) -> dict:
+        ms, n, fl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().kg_mlp_timing_read(self._m, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)))
+        return {"gemm_ms": ms.value, "gemm_launches": n.value, "gemm_flop": fl.value}
 
 
 def mlp_gemm_test(a_dev, b_dev, out_dev):

@@ -457,6 +457,11 @@ struct kg_mlp {
     size_t part_bytes = 0;
     std::vector<void*> batch_allocs;
     int64_t launches = 0;
+    // CUDA-event timing of the tensor-core GEMM launches
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gemm_events;
+    double gemm_flop = 0.0;
+    int64_t gemm_launches = 0;
 };
 
 namespace {
@@ -529,8 +534,21 @@ kg_status launch_gemm(kg_mlp* m, const GemmArgs& g, int64_t m_tiles, int splits)
                                          kGemmSmem));
         configured = true;
     }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (m->timing) {
+        KG_CUDA_TRY(cudaEventCreate(&e0));
+        KG_CUDA_TRY(cudaEventCreate(&e1));
+        KG_CUDA_TRY(cudaEventRecord(e0, m->stream));
+    }
     umma_gemm_kernel<EPI><<<dim3((unsigned)m_tiles, (unsigned)splits), kGemmThreads, kGemmSmem, m->stream>>>(g);
     KG_CUDA_TRY(cudaGetLastError());
+    if (m->timing) {
+        KG_CUDA_TRY(cudaEventRecord(e1, m->stream));
+        m->gemm_events.push_back({e0, e1});
+        // 2 M N K per CTA tile (M = 128, N = 256, K = 64 per block)
+        m->gemm_flop += 2.0 * BM * BN * (double)BK * g.k_atoms * (double)m_tiles * splits;
+        m->gemm_launches++;
+    }
     m->launches++;
     return KG_OK;
 }
@@ -771,6 +789,35 @@ kg_status kg_mlp_train_step(kg_mlp* m, const float* x, const float* t, int64_t n
 kg_status kg_mlp_launches(kg_mlp* m, int64_t* launches) {
     if (!m || !launches) return fail(KG_EINVAL, "mlp: NULL argument");
     *launches = m->launches;
+    return KG_OK;
+}
+
+kg_status kg_mlp_timing_enable(kg_mlp* m, int enable) {
+    if (!m) return fail(KG_EINVAL, "mlp: NULL argument");
+    cudaStreamSynchronize(m->stream);
+    for (auto& e : m->gemm_events) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    m->gemm_events.clear();
+    m->gemm_flop = 0.0;
+    m->gemm_launches = 0;
+    m->timing = enable != 0;
+    return KG_OK;
+}
+
+kg_status kg_mlp_timing_read(kg_mlp* m, double* gemm_ms, int64_t* gemm_launches, double* gemm_flop) {
+    if (!m) return fail(KG_EINVAL, "mlp: NULL argument");
+    KG_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    double ms = 0.0;
+    for (auto& e : m->gemm_events) {
+        float t = 0;
+        KG_CUDA_TRY(cudaEventElapsedTime(&t, e.first, e.second));
+        ms += t;
+    }
+    if (gemm_ms) *gemm_ms = ms;
+    if (gemm_launches) *gemm_launches = m->gemm_launches;
+    if (gemm_flop) *gemm_flop = m->gemm_flop;
     return KG_OK;
 }
 

@@ -68,3 +68,20 @@ def test_adam_training_reduces_loss():
         last = net.train_step(x, t, 1e-3)
     assert last < 0.1 * first, (first, last)
     assert np.all(np.isfinite(net.params()))
+
+
+def test_surrogate_learns_method_sigma_and_is_faster():
+    """Reduced surrogate workflow: sigma^GK(E, t) surfaces from the method for 10 vacancy
+    concentrations x 3 disorder seeds on 64 x 64-cell sheets; train on 8, predict the 2
+    held-out concentrations.  The network reproduces their ensemble-averaged surfaces
+    within 15 % (relative L2) and evaluates a surface far faster than one method run."""
+    from oracle import mlp as om
+    from paper_1307_0288_gb300 import surrogate as sg
+    grid = sg.Grid(cells=(64, 64), n_moments=256, n_times=16, n_energies=41)
+    ds = sg.generate(grid, n_conc=10, seeds=3, held_out=[3, 6])
+    net, info = sg.train(ds, om.init_params(11), epochs=60, batch=1024, lr=3e-3)
+    assert info["losses"][-1] < 0.05 * info["losses"][0]
+    res = sg.evaluate(ds, net, info["scale"])
+    for r in res:
+        assert r["surrogate_rel_err"] < 0.15, r
+        assert r["surrogate_seconds"] < 0.1 * np.mean(ds.method_seconds), r
