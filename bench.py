@@ -40,6 +40,7 @@ TOL = 1e-15
 WORKLOADS = {
     "msd-sheet-2048x1024-vac0.5pct-R4-M3000-dt2": ((1024, 512), 0.005, 4, 3000, 2.0, "f64"),
     "msd-sheet-4096x2048-vac1pct-R8-M6000-dt2-c64": ((2048, 1024), 0.01, 8, 6000, 2.0, "c64"),
+    "msd-sheet-2048x1024-vac1pct-R8-M3000-dt2-c64": ((1024, 512), 0.01, 8, 3000, 2.0, "c64"),
 }
 DEFAULT_WORKLOAD = "msd-sheet-2048x1024-vac0.5pct-R4-M3000-dt2"
 BATCHED_WORKLOAD = "dos-zgnr16-uneven-anderson-R64-M2000-batched"
@@ -449,11 +450,11 @@ def run_surrogate(args):
     training step on 65,536 samples."""
     import torch
     import paper_1307_0288_gb300 as kg
-    from oracle import mlp as om   # only for the parameter initialisation rule
+    from paper_1307_0288_gb300 import surrogate
 
     torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
     n = 1 << 20
-    net = kg.Mlp(om.init_params(1).astype(np.float32))
+    net = kg.Mlp(surrogate.init_params(1))
     g = torch.Generator(device="cuda").manual_seed(5)
     x = (torch.rand((n, 3), generator=g, device="cuda") * 2 - 1).contiguous()
     y = torch.zeros(n, dtype=torch.float32, device="cuda")

@@ -42,6 +42,17 @@ class Grid:
         return np.arange(self.n_times) * self.dt * HBAR_EV_FS / self.gamma0_ev
 
 
+def init_params(seed: int, hidden: int = 256) -> np.ndarray:
+    """Initial FP32 parameters in the library's flat layout: weights uniform in
+    +-1/sqrt(fan_in), biases zero."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in [(hidden, 3), (hidden, hidden), (hidden, hidden), (hidden, hidden), (1, hidden)]:
+        b = 1.0 / np.sqrt(fan_in)
+        parts += [rng.uniform(-b, b, size=fan_out * fan_in), np.zeros(fan_out)]
+    return np.concatenate(parts).astype(np.float32)
+
+
 def sigma_surface(conc: float, seed: int, grid: Grid, precision: int = KG_C64):
     """sigma^GK(E, t_m) [N_c][n_E] in e^2/h for one disorder realisation (one vector),
     and the seconds the method took."""
@@ -161,8 +172,6 @@ def main(argv=None):
     import argparse
     import json
 
-    from oracle import mlp as om
-
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=None)
     ap.add_argument("--n-conc", type=int, default=40)
@@ -173,7 +182,7 @@ def main(argv=None):
     t0 = time.perf_counter()
     ds = generate(grid, n_conc=a.n_conc, seeds=a.seeds)
     gen_s = time.perf_counter() - t0
-    net, info = train(ds, om.init_params(1), epochs=a.epochs)
+    net, info = train(ds, init_params(1), epochs=a.epochs)
     res = evaluate(ds, net, info["scale"])
     summary = {
         "grid": {"sites": 4 * grid.cells[0] * grid.cells[1], "moments": grid.n_moments,
