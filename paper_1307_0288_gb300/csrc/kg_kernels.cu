@@ -133,29 +133,51 @@ __device__ __forceinline__ float2 mk<float>(float x, float y) { return make_floa
 // (both real for Hermitian H~).  The kernel computes phi_{n+1} = 2H~phi_n - phi_{n-1}
 // (first step: phi_1 = H~ phi_0) and the two per-block partial sums.
 // --------------------------------------------------------------------------------
+// Items processed per loop iteration: the FP32 kernels are bound by memory latency
+// (neighbour indices, then the gathered values), so two independent items are loaded
+// before any arithmetic; the FP64 kernels are bound by the DP pipe and keep one.
+template <typename T>
+constexpr int kIlp = sizeof(T) == sizeof(float) ? 2 : 1;
+
 template <typename T, int R, bool ONSITE, bool FIRST>
 __global__ void __launch_bounds__(kThreads) kpm_sym_kernel(DevH H, const vec2_t<T>* __restrict__ cur,
                                                            const vec2_t<T>* prev, vec2_t<T>* out,
                                                            double* __restrict__ partial) {
+    constexpr int U = kIlp<T>;
     const int64_t n_items = H.n * R;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     const int r = threadIdx.x & (R - 1);
     const T c = (T)(FIRST ? H.h : 2.0 * H.h);
     Acc<T> a0, a1;
-    for (int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x; w < n_items; w += stride) {
-        const int64_t n = w / R;
-        const Nbr<T> g = gather<T, R>(H.idx, H.istride, n, r, cur);
-        T e = 0;
-        if constexpr (ONSITE) e = (T)((FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n));
-        vec2_t<T> z = mk<T>(0, 0);
-        if constexpr (!FIRST) z = prev[w];
-        const T yr = hop<T>(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
-        const T yi = hop<T>(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
-        out[w] = mk<T>(yr, yi);
-        a0.add_prod(g.x.x, g.x.x);
-        a0.add_prod(g.x.y, g.x.y);
-        a1.add_prod(yr, g.x.x);
-        a1.add_prod(yi, g.x.y);
+    for (int64_t w0 = (int64_t)blockIdx.x * kThreads + threadIdx.x; w0 < n_items; w0 += U * stride) {
+        Nbr<T> g[U];
+        vec2_t<T> z[U];
+        T e[U];
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            const int64_t w = w0 + k * stride;
+            if (w < n_items) {
+                const int64_t n = w / R;
+                g[k] = gather<T, R>(H.idx, H.istride, n, r, cur);
+                e[k] = 0;
+                if constexpr (ONSITE) e[k] = (T)((FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n));
+                z[k] = mk<T>(0, 0);
+                if constexpr (!FIRST) z[k] = prev[w];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            const int64_t w = w0 + k * stride;
+            if (w < n_items) {
+                const T yr = hop<T>(c, g[k].a.x, g[k].b.x, g[k].c.x, e[k], g[k].x.x, z[k].x, ONSITE);
+                const T yi = hop<T>(c, g[k].a.y, g[k].b.y, g[k].c.y, e[k], g[k].x.y, z[k].y, ONSITE);
+                out[w] = mk<T>(yr, yi);
+                a0.add_prod(g[k].x.x, g[k].x.x);
+                a0.add_prod(g[k].x.y, g[k].x.y);
+                a1.add_prod(yr, g[k].x.x);
+                a1.add_prod(yi, g[k].x.y);
+            }
+        }
     }
     double acc[2] = {a0.value(), a1.value()};
     block_reduce<R, 2>(acc, partial + (int64_t)blockIdx.x * R * 2);
@@ -172,32 +194,48 @@ __global__ void __launch_bounds__(kThreads) kpm_gen_kernel(DevH H, const vec2_t<
                                                            const vec2_t<T>* prev, vec2_t<T>* out,
                                                            double* __restrict__ partial) {
     constexpr int NACC = FIRST ? 4 : 2;
+    constexpr int U = kIlp<T>;
     const int64_t n_items = H.n * R;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     const int r = threadIdx.x & (R - 1);
     const T c = (T)(FIRST ? H.h : 2.0 * H.h);
     Acc<T> a[NACC];
-    for (int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x; w < n_items; w += stride) {
-        const int64_t n = w / R;
-        const Nbr<T> g = gather<T, R>(H.idx, H.istride, n, r, cur);
-        T e = 0;
-        if constexpr (ONSITE) e = (T)((FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n));
-        vec2_t<T> z = mk<T>(0, 0);
-        if constexpr (!FIRST) z = prev[w];
-        const T yr = hop<T>(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
-        const T yi = hop<T>(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
-        out[w] = mk<T>(yr, yi);
-        const vec2_t<T> l = __ldg(L + w);
-        // <L|y> = (l.x y.x + l.y y.y) + i (l.x y.y - l.y y.x)
-        a[0].add_prod(l.x, yr);
-        a[0].add_prod(l.y, yi);
-        a[1].add_prod(l.x, yi);
-        a[1].add_prod(-l.y, yr);
-        if constexpr (FIRST) {
-            a[2].add_prod(l.x, g.x.x);
-            a[2].add_prod(l.y, g.x.y);
-            a[3].add_prod(l.x, g.x.y);
-            a[3].add_prod(-l.y, g.x.x);
+    for (int64_t w0 = (int64_t)blockIdx.x * kThreads + threadIdx.x; w0 < n_items; w0 += U * stride) {
+        Nbr<T> g[U];
+        vec2_t<T> z[U], l[U];
+        T e[U];
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            const int64_t w = w0 + k * stride;
+            if (w < n_items) {
+                const int64_t n = w / R;
+                g[k] = gather<T, R>(H.idx, H.istride, n, r, cur);
+                e[k] = 0;
+                if constexpr (ONSITE) e[k] = (T)((FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n));
+                z[k] = mk<T>(0, 0);
+                if constexpr (!FIRST) z[k] = prev[w];
+                l[k] = __ldg(L + w);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            const int64_t w = w0 + k * stride;
+            if (w < n_items) {
+                const T yr = hop<T>(c, g[k].a.x, g[k].b.x, g[k].c.x, e[k], g[k].x.x, z[k].x, ONSITE);
+                const T yi = hop<T>(c, g[k].a.y, g[k].b.y, g[k].c.y, e[k], g[k].x.y, z[k].y, ONSITE);
+                out[w] = mk<T>(yr, yi);
+                // <L|y> = (l.x y.x + l.y y.y) + i (l.x y.y - l.y y.x)
+                a[0].add_prod(l[k].x, yr);
+                a[0].add_prod(l[k].y, yi);
+                a[1].add_prod(l[k].x, yi);
+                a[1].add_prod(-l[k].y, yr);
+                if constexpr (FIRST) {
+                    a[2].add_prod(l[k].x, g[k].x.x);
+                    a[2].add_prod(l[k].y, g[k].x.y);
+                    a[3].add_prod(l[k].x, g[k].x.y);
+                    a[3].add_prod(-l[k].y, g[k].x.x);
+                }
+            }
         }
     }
     double acc[NACC];

@@ -253,6 +253,276 @@ __global__ void __launch_bounds__(kGemmThreads, 1) umma_gemm_kernel(GemmArgs g) 
     }
 }
 
+// ------------------------------------------------------------------- persistent inference GEMM
+//
+// Activations for inference use a core-matrix-tiled layout: the 128-row tile t of an
+// [rows][256] matrix is stored contiguously (64 KB) as [32 k-chunks][128 rows][8 values],
+// i.e. element (row, k) at t*32768 + ((k/8)*128 + row%128)*8 + k%8.  A 64-wide K block of
+// a tile is then one contiguous 16 KB run that a single cp.async.bulk copies into the
+// canonical K-major no-swizzle shared-memory layout (core matrix = 8 rows x 16 B; LBO =
+// distance between core matrices along K, SBO = between 8-row groups), and every
+// epilogue store of 8 values per row is one 16-byte word, coalesced across a warp.
+// The weights use the same layout with 256 rows: [32 k-chunks][256 rows][8].
+
+__host__ __device__ constexpr int64_t tiled_index(int64_t row, int col) {
+    return (row >> 7) * (128 * H) + ((int64_t)(col >> 3) * 128 + (row & 127)) * 8 + (col & 7);
+}
+
+constexpr int kPThreads = 320;          // warps 0-7 epilogue, 8 loads, 9 MMA + TMEM
+constexpr int kPWBytes = H * H * 2;     // 128 KB
+constexpr int kPAtomBytes = BM * BK * 2;   // 16 KB
+constexpr int kPSlots = 4;
+constexpr int kPSmem = kPWBytes + kPSlots * kPAtomBytes + 2 * 2 * BM * 4 + 256 + 1024;
+
+struct PArgs {
+    const __nv_bfloat16* a_tiled;   // [n_tiles][32][128][8]
+    int64_t n_tiles;
+    const __nv_bfloat16* w_tiled;   // [32][256][8]
+    const float* bias;              // [256]
+    __nv_bfloat16* out_tiled;       // next layer's activations (null when the output is fused)
+    const float* w5;                // fused output layer: y = w5 . GELU(z) + b5
+    float b5;
+    float* y;
+    int64_t n_valid;
+    int* error;
+};
+
+// No-swizzle K-major descriptor (layout type 0) with the given LBO / SBO in bytes.
+__device__ __forceinline__ uint64_t ns_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ bool pwait(uint32_t bar, uint32_t parity, volatile int* abort) {
+    for (long long i = 0; i < kWaitLimit; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (*abort) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <bool FUSE_OUT>
+__global__ void __launch_bounds__(kPThreads, 1) umma_persistent_kernel(PArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* base_ptr = smem_raw + (base - raw);
+    const uint32_t sW = base, sA = base + kPWBytes;
+    float* ypart = (float*)(base_ptr + kPWBytes + kPSlots * kPAtomBytes);   // [2 acc][2 halves][128]
+    const uint32_t bars = base + kPWBytes + kPSlots * kPAtomBytes + 2 * 2 * BM * 4;
+    const uint32_t w_full = bars, a_full = bars + 8, a_empty = bars + 8 * 5, acc_full = bars + 8 * 9,
+                   acc_empty = bars + 8 * 11;
+    uint32_t* tmem_slot = (uint32_t*)(base_ptr + kPWBytes + kPSlots * kPAtomBytes + 2 * 2 * BM * 4 + 8 * 13);
+    __shared__ volatile int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        s_abort = 0;
+        mbar_init(w_full, 1);
+        for (int a = 0; a < kPSlots; a++) {
+            mbar_init(a_full + 8 * a, 1);
+            mbar_init(a_empty + 8 * a, 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(acc_full + 8 * b, 1);
+            mbar_init(acc_empty + 8 * b, 8);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 9) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(2 * BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    auto give_up = [&]() {
+        atomicExch(p.error, 1);
+        s_abort = 1;
+    };
+
+    if (warp == 8 && lane == 0) {
+        // loads: the weights once, then the four K blocks of every tile of this CTA
+        expect_tx(w_full, kPWBytes);
+        for (int c = 0; c < kPWBytes / kPAtomBytes; c++)
+            bulk_g2s(sW + c * kPAtomBytes, (const uint8_t*)p.w_tiled + (size_t)c * kPAtomBytes, kPAtomBytes, w_full);
+        int j = 0, last_slot = -1, last_use = 0;
+        for (int64_t t = blockIdx.x; t < p.n_tiles && !s_abort; t += gridDim.x, j++) {
+            for (int a = 0; a < kPSlots; a++) {
+                if (j > 0 && !pwait(a_empty + 8 * a, (j - 1) & 1, &s_abort)) {
+                    give_up();
+                    break;
+                }
+                expect_tx(a_full + 8 * a, kPAtomBytes);
+                bulk_g2s(sA + a * kPAtomBytes, (const uint8_t*)p.a_tiled + ((size_t)t * 4 + a) * kPAtomBytes,
+                         kPAtomBytes, a_full + 8 * a);
+                last_slot = a;
+                last_use = j;
+            }
+        }
+        // no copy may still be landing when the CTA exits (bounded, ignores the abort flag)
+        volatile int never = 0;
+        if (!pwait(w_full, 0, &never)) atomicExch(p.error, 1);
+        if (last_slot >= 0 && !pwait(a_full + 8 * last_slot, last_use & 1, &never)) atomicExch(p.error, 1);
+    } else if (warp == 9 && lane == 0) {
+        // MMA issue: D[acc] = A_tile (128 x 256) * W^T, four K blocks of four K=16 steps
+        if (!pwait(w_full, 0, &s_abort)) give_up();
+        int j = 0;
+        uint32_t last_bar = 0, last_parity = 0;   // barrier of the last commit issued
+        for (int64_t t = blockIdx.x; t < p.n_tiles && !s_abort; t += gridDim.x, j++) {
+            const int acc = j & 1;
+            if (j >= 2 && !pwait(acc_empty + 8 * acc, ((j >> 1) - 1) & 1, &s_abort)) {
+                give_up();
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            bool ok = true;
+            for (int a = 0; a < kPSlots && ok; a++) {
+                if (!pwait(a_full + 8 * a, j & 1, &s_abort)) {
+                    give_up();
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int s = 0; s < BK / 16; s++) {
+                    // A: K block a, k-chunks 2s, 2s+1 (LBO = 128 rows x 16 B, SBO = 8 rows x 16 B)
+                    const uint64_t ad = ns_desc(sA + a * kPAtomBytes + s * 2 * BM * 16, BM * 16, 128);
+                    // B: global k-chunks 8a + 2s, +1 of the 256-row weight tile
+                    const uint64_t bd = ns_desc(sW + (a * 8 + 2 * s) * BN * 16, BN * 16, 128);
+                    const uint32_t accum = (a > 0 || s > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + acc * BN),
+                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(accum)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 a_empty + 8 * a)
+                             : "memory");
+                last_bar = a_empty + 8 * a;
+                last_parity = j & 1;
+            }
+            if (!ok) break;
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             acc_full + 8 * acc)
+                         : "memory");
+            last_bar = acc_full + 8 * acc;
+            last_parity = (j >> 1) & 1;
+        }
+        // every MMA issued must be complete before the TMEM is freed (bounded)
+        volatile int never = 0;
+        if (last_bar && !pwait(last_bar, last_parity, &never)) atomicExch(p.error, 1);
+    } else if (warp < 8) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows) and columns of half w / 4
+        const int quarter = warp & 3, half = warp >> 2;
+        const int rl = quarter * 32 + lane;
+        int j = 0;
+        for (int64_t t = blockIdx.x; t < p.n_tiles; t += gridDim.x, j++) {
+            const int acc = j & 1;
+            const bool ok = pwait(acc_full + 8 * acc, (j >> 1) & 1, &s_abort);
+            if (!ok) give_up();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int64_t row = t * BM + rl;
+            float ysum = 0.0f;
+            if (ok) {
+#pragma unroll 1
+                for (int cb = 0; cb < 4; cb++) {
+                    const int col0 = half * 128 + cb * 32;
+                    uint32_t v[32];
+                    KG_TMEM_LD32(tmem + acc * BN + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0, v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int c8 = 0; c8 < 4; c8++) {
+                        uint32_t packed[4];
+#pragma unroll
+                        for (int e = 0; e < 8; e += 2) {
+                            const int col = col0 + c8 * 8 + e;
+                            const float g0 = gelu(__uint_as_float(v[c8 * 8 + e]) + p.bias[col]);
+                            const float g1 = gelu(__uint_as_float(v[c8 * 8 + e + 1]) + p.bias[col + 1]);
+                            if constexpr (FUSE_OUT) {
+                                ysum = fmaf(__bfloat162float(__float2bfloat16_rn(g0)), p.w5[col], ysum);
+                                ysum = fmaf(__bfloat162float(__float2bfloat16_rn(g1)), p.w5[col + 1], ysum);
+                            } else {
+                                const __nv_bfloat162 b2 = __floats2bfloat162_rn(g0, g1);
+                                packed[e >> 1] = *(const uint32_t*)&b2;
+                            }
+                        }
+                        if constexpr (!FUSE_OUT) {
+                            const int chunk = (col0 >> 3) + c8;
+                            uint4* dst = (uint4*)(p.out_tiled + t * (int64_t)(BM * H) + ((int64_t)chunk * BM + rl) * 8);
+                            *dst = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty + 8 * acc);
+            if constexpr (FUSE_OUT) {
+                ypart[(acc * 2 + half) * BM + rl] = ysum;
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+                if (half == 0 && row < p.n_valid && ok)
+                    p.y[row] = ypart[(acc * 2) * BM + rl] + ypart[(acc * 2 + 1) * BM + rl] + p.b5;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 9) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+    }
+}
+
+// Layer 1 for inference, written in the tiled layout (k runs over the tiled order, so
+// consecutive threads write consecutive 2-byte words).
+__global__ void layer1_tiled_kernel(const float* __restrict__ x, int64_t n_valid, int64_t rows,
+                                    const float* __restrict__ p, __nv_bfloat16* __restrict__ a) {
+    const int64_t total = rows * H;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t tile = k / (BM * H);
+        const int rem = (int)(k % (BM * H));
+        const int c = (rem / (BM * 8)) * 8 + (rem & 7);
+        const int64_t r = tile * BM + (rem / 8) % BM;
+        float v = p[kOffB1 + c];
+        if (r < n_valid) {
+            v = fmaf(p[kOffW1 + c * 3 + 0], x[r * 3 + 0], v);
+            v = fmaf(p[kOffW1 + c * 3 + 1], x[r * 3 + 1], v);
+            v = fmaf(p[kOffW1 + c * 3 + 2], x[r * 3 + 2], v);
+        }
+        a[k] = __float2bfloat16_rn(gelu(v));
+    }
+}
+
 // ------------------------------------------------------------------- CUDA-core kernels
 
 // Layer 1 (K = 3): z = W1 x + b1, a = GELU(z); rows >= n_valid use x = 0.
@@ -411,7 +681,7 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
 
 // BF16 copies of W2..W4 ([out][in]) and their transposes ([in][out]).
 __global__ void cast_weights_kernel(const float* __restrict__ p, __nv_bfloat16* __restrict__ w,
-                                    __nv_bfloat16* __restrict__ wt) {
+                                    __nv_bfloat16* __restrict__ wt, __nv_bfloat16* __restrict__ wtile) {
     const int64_t total = 3 * (int64_t)H * H;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(k / (H * H));
@@ -420,6 +690,8 @@ __global__ void cast_weights_kernel(const float* __restrict__ p, __nv_bfloat16* 
         const __nv_bfloat16 b = __float2bfloat16_rn(p[layer_w(l + 2) + rem]);
         w[k] = b;
         wt[(int64_t)l * H * H + (int64_t)i * H + o] = b;
+        // tiled: [32 k-chunks][256 rows][8], row = output unit o, k = input i
+        wtile[(int64_t)l * H * H + ((int64_t)(i >> 3) * H + o) * 8 + (i & 7)] = b;
     }
 }
 
@@ -440,6 +712,9 @@ struct kg_mlp {
     float* adam_v = nullptr;
     __nv_bfloat16* w = nullptr;    // [3][H][H]
     __nv_bfloat16* wt = nullptr;   // [3][H][H]
+    __nv_bfloat16* wtile = nullptr;   // [3][32][H][8] (tiled for the persistent kernel)
+    __nv_bfloat16* at_inf[2] = {nullptr, nullptr};   // tiled inference activations
+    int64_t inf_cap = 0;
     int* error = nullptr;
     double* loss = nullptr;
     int64_t step = 0;
@@ -580,6 +855,72 @@ kg_status mlp_forward(kg_mlp* m, int64_t n_valid, int64_t rows, bool train) {
     return KG_OK;
 }
 
+// Inference: layer 1 (CUDA cores, tiled output), layers 2-3 with the persistent tcgen05
+// kernel, layer 4 with the output layer fused into its epilogue.
+kg_status mlp_infer(kg_mlp* m, int64_t n_valid, int64_t rows) {
+    if (rows > m->inf_cap) {
+        for (auto& q : m->at_inf) {
+            if (q) cudaFree(q);
+            q = nullptr;
+        }
+        m->inf_cap = 0;
+        for (auto& q : m->at_inf)
+            if (cudaMalloc(&q, rows * H * sizeof(__nv_bfloat16)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(KG_ENOMEM, "mlp: device allocation failed");
+            }
+        m->inf_cap = rows;
+    }
+    static bool configured = false;
+    if (!configured) {
+        KG_CUDA_TRY(cudaFuncSetAttribute(umma_persistent_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPSmem));
+        KG_CUDA_TRY(cudaFuncSetAttribute(umma_persistent_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPSmem));
+        configured = true;
+    }
+    const int grid1 = std::max(1, std::min<int>(sm_count() * 8, (int)((rows * H + 255) / 256)));
+    layer1_tiled_kernel<<<grid1, 256, 0, m->stream>>>(m->x, n_valid, rows, m->params, m->at_inf[0]);
+    KG_CUDA_TRY(cudaGetLastError());
+    m->launches++;
+    const int64_t n_tiles = rows / BM;
+    const int grid = (int)std::min<int64_t>(n_tiles, sm_count());
+    for (int l = 2; l <= 4; l++) {
+        PArgs pa{};
+        pa.a_tiled = m->at_inf[(l - 2) & 1];
+        pa.n_tiles = n_tiles;
+        pa.w_tiled = m->wtile + (int64_t)(l - 2) * H * H;
+        pa.bias = m->params + layer_b(l);
+        pa.out_tiled = l < 4 ? m->at_inf[(l - 1) & 1] : nullptr;
+        pa.w5 = m->params + kOffW5;
+        pa.y = m->y;
+        pa.n_valid = n_valid;
+        pa.error = m->error;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (m->timing) {
+            KG_CUDA_TRY(cudaEventCreate(&e0));
+            KG_CUDA_TRY(cudaEventCreate(&e1));
+            KG_CUDA_TRY(cudaEventRecord(e0, m->stream));
+        }
+        if (l < 4) umma_persistent_kernel<false><<<grid, kPThreads, kPSmem, m->stream>>>(pa);
+        else {
+            // b5 is read on the host side of the launch: copy it once per call
+            float b5 = 0.0f;
+            KG_CUDA_TRY(cudaMemcpyAsync(&b5, m->params + kOffB5, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+            KG_CUDA_TRY(cudaStreamSynchronize(m->stream));
+            pa.b5 = b5;
+            umma_persistent_kernel<true><<<grid, kPThreads, kPSmem, m->stream>>>(pa);
+        }
+        KG_CUDA_TRY(cudaGetLastError());
+        if (m->timing) {
+            KG_CUDA_TRY(cudaEventRecord(e1, m->stream));
+            m->gemm_events.push_back({e0, e1});
+            m->gemm_flop += 2.0 * BM * BN * (double)H * (double)n_tiles;
+            m->gemm_launches++;
+        }
+        m->launches++;
+    }
+    return KG_OK;
+}
+
 kg_status check_mlp_error(kg_mlp* m) {
     int err = 0;
     KG_CUDA_TRY(cudaMemcpyAsync(&err, m->error, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
@@ -689,7 +1030,7 @@ kg_status kg_mlp_create(const float* params, void* cuda_stream, kg_mlp** out) {
     };
     const size_t pb = kParams * sizeof(float);
     void* p = nullptr;
-    if (cudaMalloc(&p, 4 * pb + 2 * 3 * H * H * sizeof(__nv_bfloat16) + 256) != cudaSuccess) {
+    if (cudaMalloc(&p, 4 * pb + 3 * 3 * H * H * sizeof(__nv_bfloat16) + 256) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(KG_ENOMEM, "mlp: device allocation failed"));
     }
@@ -700,6 +1041,7 @@ kg_status kg_mlp_create(const float* params, void* cuda_stream, kg_mlp** out) {
     m->adam_v = (float*)(c + 3 * pb);
     m->w = (__nv_bfloat16*)(c + ((4 * pb + 255) & ~(size_t)255));
     m->wt = m->w + 3 * H * H;
+    m->wtile = m->wt + 3 * H * H;
     void* q = nullptr;
     if (cudaMalloc(&q, 256) != cudaSuccess) return bail(fail(KG_ENOMEM, "mlp: device allocation failed"));
     m->error = (int*)q;
@@ -709,7 +1051,7 @@ kg_status kg_mlp_create(const float* params, void* cuda_stream, kg_mlp** out) {
     if (cudaMemcpyAsync(m->params, params, pb, is_dev(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                         m->stream) != cudaSuccess)
         return bail(fail(KG_ECUDA, "mlp: parameter upload failed"));
-    cast_weights_kernel<<<256, 256, 0, m->stream>>>(m->params, m->w, m->wt);
+    cast_weights_kernel<<<256, 256, 0, m->stream>>>(m->params, m->w, m->wt, m->wtile);
     if (cudaStreamSynchronize(m->stream) != cudaSuccess)
         return bail(fail(KG_ECUDA, std::string("mlp: ") + cudaGetErrorString(cudaGetLastError())));
     *out = m;
@@ -720,6 +1062,8 @@ void kg_mlp_destroy(kg_mlp* m) {
     if (!m) return;
     cudaStreamSynchronize(m->stream);
     mlp_free_batch(m);
+    for (auto q : m->at_inf)
+        if (q) cudaFree(q);
     if (m->params) cudaFree(m->params);
     if (m->error) cudaFree(m->error);
     delete m;
@@ -737,11 +1081,7 @@ kg_status kg_mlp_forward(kg_mlp* m, const float* x, int64_t n, float* y) {
     if (!m || !x || !y || n < 1) return fail(KG_EINVAL, "mlp: bad arguments");
     const int64_t rows = padded(n);
     KG_TRY(stage_batch(m, x, nullptr, n, rows, false));
-    KG_TRY(mlp_forward(m, n, rows, false));
-    out_kernel<<<(int)std::min<int64_t>(4096, (rows + 7) / 8), 256, 0, m->stream>>>(
-        m->a[3], nullptr, n, rows, m->params, nullptr, m->y, nullptr, nullptr, nullptr);
-    KG_CUDA_TRY(cudaGetLastError());
-    m->launches++;
+    KG_TRY(mlp_infer(m, n, rows));
     KG_TRY(check_mlp_error(m));
     KG_CUDA_TRY(cudaMemcpyAsync(y, m->y, n * sizeof(float), cudaMemcpyDefault, m->stream));
     KG_CUDA_TRY(cudaStreamSynchronize(m->stream));
@@ -775,7 +1115,7 @@ kg_status kg_mlp_train_step(kg_mlp* m, const float* x, const float* t, int64_t n
     adam_kernel<<<256, 256, 0, m->stream>>>(m->params, m->grad, m->adam_m, m->adam_v, kParams, lr, b1, b2, 1e-8f,
                                             c1, c2);
     KG_CUDA_TRY(cudaGetLastError());
-    cast_weights_kernel<<<256, 256, 0, m->stream>>>(m->params, m->w, m->wt);
+    cast_weights_kernel<<<256, 256, 0, m->stream>>>(m->params, m->w, m->wt, m->wtile);
     KG_CUDA_TRY(cudaGetLastError());
     m->launches += 2;
     KG_TRY(check_mlp_error(m));
