@@ -143,6 +143,13 @@ kg_status kg_vac(kg_hamiltonian* h, const kg_run* run, const double* phi, double
  * phi: host or device [N][R][2].  mu_out: host or device [R][N_c][M][2]. */
 kg_status kg_msd(kg_hamiltonian* h, const kg_run* run, const double* phi, double* mu_out);
 
+/* Fourier moments F_n = <phi|U(n dtau)|phi>, n = -N_m .. N_m (Eq. 25, Algorithm 4), with
+ * the Nyquist step dtau = pi hbar for the scaled Hamiltonian (Sec. 4.2), i.e. U(dtau) =
+ * exp(-i pi H~) applied n times forward and n times backward.  run->n_moments is N_m,
+ * run->bessel_tol truncates the series of U(dtau); KG_FP64 only.
+ * phi: host or device [N][R][2].  f_out: host or device [R][2 N_m + 1][2], index n + N_m. */
+kg_status kg_ftm_dos_moments(kg_hamiltonian* h, const kg_run* run, const double* phi, double* f_out);
+
 #define KG_OP_H 0    /* out = H~ in                                  (Algorithm 8) */
 #define KG_OP_XH 1   /* out = [X, H~] in, (X_n - X_m) H~_nm, in nm    (Eq. 15)     */
 #define KG_OP_V 2    /* out = V in = (i/hbar)[H, X] in, in nm/fs      (Eq. 15)     */
@@ -299,6 +306,14 @@ kg_status kg_jackson(int n_moments, double* g_out);
  * in 1/(eV nm^2) times the moments' unit. */
 kg_status kg_kpm_sum(const double* mu, int n_sets, int n_moments, const double* energies_ev,
                      int n_e, double emax_ev, double area_nm2, double* out);
+
+/* FTM density of states, Eq. 22 with the Hanning window of Eq. 28 (w_n = (1 +
+ * cos(pi n/(N_m+1)))/2) and dtau = pi hbar / E_max:
+ *   out[s][e] = 1/(E_max Omega) sum_n w_n Re[exp(i pi n E/E_max) f[s][n + N_m]].
+ * f: host [n_sets][2 N_m + 1][2] (complex moments, averaged over vectors); out: host
+ * [n_sets][n_e] in 1/(eV nm^2). */
+kg_status kg_ftm_sum(const double* f, int n_sets, int n_m, const double* energies_ev, int n_e,
+                     double emax_ev, double area_nm2, double* out);
 
 #define KG_SIGMA_GK 0   /* Eq. 6: e^2 int_0^t rho C_vv dt' (trapezoid)            */
 #define KG_SIGMA_E1 1   /* Eq. 9: e^2 d(rho DX^2)/(2 dt) (central differences)    */

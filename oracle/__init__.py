@@ -65,6 +65,7 @@ def lib():
         L.ora_msd.argtypes = hargs + [P, I, I, P, I, P]
         L.ora_jackson.argtypes = [I, P]
         L.ora_kpm_sum.argtypes = [I, P, P, I, P, P]
+        L.ora_ftm_moments.argtypes = hargs + [P, P, I, P, I, P]
         L.ora_set_mutation.argtypes = [I]
         L.ora_get_mutation.restype = I
         _lib = L
@@ -241,6 +242,15 @@ def msd_moments(h: Hamiltonian, phi, n_moments: int, n_times: int,
     lib().ora_msd(*h._hargs(), _p(phi), n_moments, n_times, _p(jm), np_, _p(c))
     c = c.reshape(n_times, n_moments, 2)
     return c[..., 0] + 1j * c[..., 1]
+
+
+def ftm_moments(h: Hamiltonian, phi_l, phi_r, n_m: int, tol: float = 1e-15) -> np.ndarray:
+    """Fourier moments F_n = <phi_L|U(n dtau)|phi_R>, n = -N_m..N_m, dtau = pi hbar for H~
+    (Algorithm 4, Sec. 4.2).  Complex [2 N_m + 1], index n + N_m."""
+    jm, np_ = bessel_series(np.pi, tol)
+    l = _cvec(phi_l); r = _cvec(phi_r); f = np.zeros(2 * (2 * n_m + 1))
+    lib().ora_ftm_moments(*h._hargs(), _p(l), _p(r), n_m, _p(jm), np_, _p(f))
+    return f[0::2] + 1j * f[1::2]
 
 
 def jackson(n_moments: int) -> np.ndarray:

@@ -515,3 +515,35 @@ void ora_kpm_sum(int n_moments, const double* mu, const double* g, int n_e,
         out[q] = 2.0 / (ORA_PI * sqrt(1.0 - e[q] * e[q])) * s;
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Fourier moments (Algorithm 4, Eqs. 25 and 45)                       */
+/* ------------------------------------------------------------------ */
+
+/* F_n = <phi_L|U(n dtau)|phi_R> for n = -N_m .. N_m (output index n + N_m), with
+ * U(dtau) = exp(-i H~ tau) applied n times forward and n times backward as in
+ * Algorithm 4.  For the scaled Hamiltonian the step is dtau = pi hbar, i.e. tau = pi
+ * (Sec. 4.2).  j[] holds J_m(tau), m < np.  Output f[2 N_m + 1][2]. */
+void ora_ftm_moments(int64_t n, const int64_t* rp, const int64_t* col, const double* val,
+                     const double* disp, const double* diag, const double* phi_l,
+                     const double* phi_r, int n_m, const double* jm, int np, double* f) {
+    double* p = malloc(sizeof(double) * 2 * n);
+    double* t = malloc(sizeof(double) * 2 * n);
+    /* |phi'_R> <- |phi_R>;  F_0 <- <phi_L|phi'_R> */
+    memcpy(p, phi_r, sizeof(double) * 2 * n);
+    dot(n, phi_l, p, &f[2 * n_m], &f[2 * n_m + 1]);
+    for (int k = 1; k <= n_m; k++) {
+        /* |phi'_R> <- U(dtau)|phi'_R>;  F_k <- <phi_L|phi'_R> */
+        ora_evolve(n, rp, col, val, disp, diag, jm, np, +1, p, t);
+        memcpy(p, t, sizeof(double) * 2 * n);
+        dot(n, phi_l, p, &f[2 * (n_m + k)], &f[2 * (n_m + k) + 1]);
+    }
+    memcpy(p, phi_r, sizeof(double) * 2 * n);
+    for (int k = 1; k <= n_m; k++) {
+        /* |phi'_R> <- U^dagger(dtau)|phi'_R>;  F_{-k} <- <phi_L|phi'_R> */
+        ora_evolve(n, rp, col, val, disp, diag, jm, np, -1, p, t);
+        memcpy(p, t, sizeof(double) * 2 * n);
+        dot(n, phi_l, p, &f[2 * (n_m - k)], &f[2 * (n_m - k) + 1]);
+    }
+    free(p); free(t);
+}

@@ -67,3 +67,22 @@ def sigma_e2(rho_dx2: np.ndarray, t_fs: np.ndarray) -> np.ndarray:
     nz = t > 0
     out[nz] = rho_dx2[nz] / (2.0 * t[nz, None])
     return H_EV_FS * out
+
+
+def hanning(n_m: int) -> np.ndarray:
+    """Hanning window w_n = (1 + cos(pi n / (N_m + 1))) / 2, n = -N_m..N_m (Eq. 28)."""
+    n = np.arange(-n_m, n_m + 1)
+    return 0.5 * (1.0 + np.cos(np.pi * n / (n_m + 1)))
+
+
+def ftm_density(f, energies_ev, emax_ev: float, area_nm2: float) -> np.ndarray:
+    """Eq. (22): rho(E) = dtau / (pi hbar Omega) sum_n w_n exp(i E n dtau / hbar) F_n.
+    With H~ = H / E_max the step is dtau = pi hbar / E_max (scaled step pi), so
+    rho(E) = 1 / (E_max Omega) sum_n w_n exp(i pi n E / E_max) F_n; real part returned."""
+    f = np.asarray(f)
+    n_m = (f.shape[-1] - 1) // 2
+    n = np.arange(-n_m, n_m + 1)
+    w = hanning(n_m)
+    e = np.asarray(energies_ev) / emax_ev
+    phase = np.exp(1j * np.pi * np.outer(e, n))
+    return np.real(phase @ (w * f).T).T / (emax_ev * area_nm2)

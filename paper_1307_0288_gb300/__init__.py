@@ -81,6 +81,8 @@ ABI = [
     ("kg_batched_tuning", _I, [_P, _P, _P, _I, _P, _P]),
     ("kg_batched_release", _I, []),
     ("kg_batched_test_stall", _I, [_I]),
+    ("kg_ftm_dos_moments", _I, [_P, ctypes.POINTER(_Run), _P, _P]),
+    ("kg_ftm_sum", _I, [_P, _I, _I, _P, _I, _D, _D, _P]),
     ("kg_mlp_create", _I, [_P, _P, ctypes.POINTER(_P)]),
     ("kg_mlp_destroy", None, [_P]),
     ("kg_mlp_get_params", _I, [_P, _P]),
@@ -278,6 +280,25 @@ def msd(h: Hamiltonian, phi, n_moments: int, n_times: int, dt: float, *, bessel_
     r = _nvec(phi, h.n)
     run = _run(n_moments, r, n_times, precision, dt, bessel_tol)
     return _moments_call(lib().kg_msd, h, phi, run, (r, n_times, n_moments), out)
+
+
+def ftm_dos_moments(h: Hamiltonian, phi, n_m: int, *, bessel_tol=1e-15, out=None):
+    """kg_ftm_dos_moments -> complex [R][2 N_m + 1] (index n + N_m)."""
+    r = _nvec(phi, h.n)
+    run = _run(n_m, r, 1, KG_FP64, 1.0, bessel_tol)
+    return _moments_call(lib().kg_ftm_dos_moments, h, phi, run, (r, 2 * n_m + 1), out)
+
+
+def ftm_sum(f, energies_ev, emax_ev: float, area_nm2: float) -> np.ndarray:
+    """kg_ftm_sum: f complex [..., 2 N_m + 1] -> [..., n_E] (Eqs. 22, 28)."""
+    f = np.ascontiguousarray(f, dtype=np.complex128)
+    lead, width = f.shape[:-1], f.shape[-1]
+    e = np.ascontiguousarray(energies_ev, dtype=np.float64)
+    sets = int(np.prod(lead)) if lead else 1
+    out = np.zeros((sets, len(e)))
+    _check(lib().kg_ftm_sum(f.ctypes.data, sets, (width - 1) // 2, e.ctypes.data, len(e), float(emax_ev),
+                            float(area_nm2), out.ctypes.data))
+    return out.reshape(*lead, len(e))
 
 
 def apply(h: Hamiltonian, op: int, x, out):

@@ -220,6 +220,14 @@ struct Series {
     int np = 0;
 };
 
+static kg_status series_for_tau(double tau, double tol, Series* out) {
+    if (!(tol > 0) || !(tol < 1)) return fail(KG_EINVAL, "bessel_tol must be in (0, 1)");
+    const int cap = (int)tau + 400;
+    out->j.assign((size_t)cap, 0.0);
+    KG_TRY(bessel_series(tau, tol, cap, out->j.data(), &out->np));
+    return KG_OK;
+}
+
 static kg_status series_for(kg_hamiltonian* h, double dt, double tol, Series* out) {
     if (!(dt > 0) || !std::isfinite(dt)) return fail(KG_EINVAL, "dt must be positive");
     if (!(tol > 0) || !(tol < 1)) return fail(KG_EINVAL, "bessel_tol must be in (0, 1)");
@@ -569,6 +577,47 @@ kg_status kg_msd(kg_hamiltonian* h, const kg_run* run, const double* phi, double
     if (run->precision == KG_C64) KG_TRY(msd_impl<float>(h, R, M, NC, ser, phi));
     else KG_TRY(msd_impl<double>(h, R, M, NC, ser, phi));
     return copy_out(h, h->moments.p, mu_out, (size_t)R * NC * M * sizeof(double2));
+}
+
+kg_status kg_ftm_dos_moments(kg_hamiltonian* h, const kg_run* run, const double* phi, double* f_out) {
+    clear_error();
+    KG_TRY(check_run(h, run, false));
+    if (run->precision != KG_FP64) return fail(KG_EINVAL, "kg_ftm_dos_moments: only KG_FP64");
+    if (!phi || !f_out) return fail(KG_EINVAL, "phi and f_out must not be NULL");
+    KG_TRY(check_device(h));
+    const int R = run->n_vectors, NM = run->n_moments;
+    const int64_t width = 2 * (int64_t)NM + 1;
+    Series ser;
+    KG_TRY(series_for_tau(kPi, run->bessel_tol, &ser));   // dtau = pi hbar for H~ (Sec. 4.2)
+    // blocks: 0 phi (kept), 1 phi'_R, 2 p1 scratch, 3 series output
+    KG_TRY(ensure_vectors(h, R, 4));
+    KG_TRY(ensure_moments(h, (size_t)R * width));
+    const int grid = stream_grid(h->n * R);
+    KG_TRY(h->part_first.ensure((size_t)grid * R * 4 * sizeof(double), h->stream));
+    double* part = (double*)h->part_first.p;
+    double2* mu = (double2*)h->moments.p;
+    KG_TRY(copy_in(h, phi, V(h, 0), R));
+    // F_0 = <phi|phi>
+    KG_CUDA_TRY(launch_dot<double>(h->n * R, R, V(h, 0), V(h, 0), part, grid, mu + NM, width, h->stream));
+    h->counters.other_launches += 2;
+    for (int dir = +1; dir >= -1; dir -= 2) {
+        double2* p = V(h, 1);
+        double2* q = V(h, 3);
+        KG_CUDA_TRY(cudaMemcpyAsync(p, V(h, 0), vec_bytes(h, R), cudaMemcpyDeviceToDevice, h->stream));
+        for (int k = 1; k <= NM; k++) {
+            // |phi'_R> <- U(+-dtau)|phi'_R>  (Eq. 36: (-i)^m forward, (+i)^m backward)
+            double2* in[1] = {p};
+            double2* p1[1] = {V(h, 2)};
+            double2* acc[1] = {q};
+            KG_TRY(run_series<double>(h, R, ser, dir > 0 ? -1 : +1, 1, false, in, p1, acc, nullptr, nullptr,
+                                      nullptr));
+            std::swap(p, q);
+            KG_CUDA_TRY(launch_dot<double>(h->n * R, R, V(h, 0), p, part, grid, mu + NM + dir * k, width,
+                                           h->stream));
+            h->counters.other_launches += 2;
+        }
+    }
+    return copy_out(h, mu, f_out, (size_t)R * width * sizeof(double2));
 }
 
 kg_status kg_apply(kg_hamiltonian* h, int op, const double* in_dev, double* out_dev, int n_vectors) {

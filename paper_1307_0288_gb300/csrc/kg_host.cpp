@@ -231,6 +231,30 @@ kg_status kg_kpm_sum(const double* mu, int n_sets, int n_moments, const double* 
     return KG_OK;
 }
 
+// Eq. 22 with the Hanning window of Eq. 28 and the scaled step dtau = pi hbar / E_max:
+// rho(E) = 1 / (E_max Omega) sum_{n=-N_m}^{N_m} w_n Re[exp(i pi n E / E_max) F_n].
+kg_status kg_ftm_sum(const double* f, int n_sets, int n_m, const double* energies_ev, int n_e,
+                     double emax_ev, double area_nm2, double* out) {
+    if (!f || !energies_ev || !out || n_sets < 1 || n_m < 0 || n_e < 1 || !(emax_ev > 0) || !(area_nm2 > 0))
+        return fail(KG_EINVAL, "kg_ftm_sum: bad arguments");
+    const int width = 2 * n_m + 1;
+    for (int s = 0; s < n_sets; s++) {
+        const double* fs = f + (size_t)s * width * 2;
+        for (int e = 0; e < n_e; e++) {
+            const double x = energies_ev[e] / emax_ev;
+            double acc = 0.0;
+            for (int k = -n_m; k <= n_m; k++) {
+                const double w = 0.5 * (1.0 + std::cos(kPi * k / (n_m + 1.0)));
+                const double ph = kPi * k * x;
+                const double re = fs[2 * (k + n_m)], im = fs[2 * (k + n_m) + 1];
+                acc += w * (std::cos(ph) * re - std::sin(ph) * im);
+            }
+            out[(size_t)s * n_e + e] = acc / (emax_ev * area_nm2);
+        }
+    }
+    return KG_OK;
+}
+
 kg_status kg_conductivity(int formula, const double* density, int n_times, int n_e,
                           double dt_fs, double* out) {
     if (!density || !out || n_times < 1 || n_e < 1 || !(dt_fs > 0))

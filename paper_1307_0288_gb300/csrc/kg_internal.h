@@ -145,6 +145,11 @@ template <typename T>
 cudaError_t launch_apply(const DevH& H, int R, int op, double scale, const vec2_t<T>* in,
                          vec2_t<T>* out, cudaStream_t s);
 
+// out[r * r_stride] = <L_r|X_r> for the R vectors (partial: [grid][R][2] scratch).
+template <typename T>
+cudaError_t launch_dot(int64_t n_items, int R, const vec2_t<T>* L, const vec2_t<T>* X, double* partial,
+                       int grid, double2* out, int64_t r_stride, cudaStream_t s);
+
 // complex128 -> complex64, element-wise.
 cudaError_t launch_to_c64(const double2* in, float2* out, int64_t n_items, cudaStream_t s);
 

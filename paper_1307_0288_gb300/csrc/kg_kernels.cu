@@ -456,6 +456,32 @@ __global__ void to_c64_kernel(const double2* __restrict__ in, float2* __restrict
 }
 
 // --------------------------------------------------------------------------------
+// Inner products <L|X> of R vector pairs (Fourier moments, Algorithm 4).
+// --------------------------------------------------------------------------------
+template <typename T, int R>
+__global__ void __launch_bounds__(kThreads) dot_kernel(int64_t n_items, const vec2_t<T>* __restrict__ L,
+                                                       const vec2_t<T>* __restrict__ X,
+                                                       double* __restrict__ partial) {
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    Acc<T> a0, a1;
+    for (int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x; w < n_items; w += stride) {
+        const vec2_t<T> l = __ldg(L + w), x = __ldg(X + w);
+        a0.add_prod(l.x, x.x);
+        a0.add_prod(l.y, x.y);
+        a1.add_prod(l.x, x.y);
+        a1.add_prod(-l.y, x.x);
+    }
+    double acc[2] = {a0.value(), a1.value()};
+    block_reduce<R, 2>(acc, partial + (int64_t)blockIdx.x * R * 2);
+}
+
+__global__ void reduce_dot_kernel(const double* __restrict__ part, int grid, int R, double2* out, int64_t r_stride) {
+    __shared__ double res[kThreads];
+    reduce_blocks(part, grid, R, 2, res);
+    if (threadIdx.x < R) out[threadIdx.x * r_stride] = make_double2(res[threadIdx.x * 2], res[threadIdx.x * 2 + 1]);
+}
+
+// --------------------------------------------------------------------------------
 // Launchers: runtime (R, flags) -> template instantiation.
 // --------------------------------------------------------------------------------
 
@@ -612,6 +638,16 @@ cudaError_t launch_apply(const DevH& H, int R, int op, double scale, const vec2_
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_dot(int64_t n_items, int R, const vec2_t<T>* L, const vec2_t<T>* X, double* partial, int grid,
+                       double2* out, int64_t r_stride, cudaStream_t s) {
+    KG_DISPATCH_R(R, dot_kernel<T, RR><<<grid, kThreads, 0, s>>>(n_items, L, X, partial));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reduce_dot_kernel<<<1, kThreads, 0, s>>>(partial, grid, R, out, r_stride);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_to_c64(const double2* in, float2* out, int64_t n_items, cudaStream_t s) {
     to_c64_kernel<<<stream_grid(n_items), kThreads, 0, s>>>(in, out, n_items);
     return cudaGetLastError();
@@ -627,7 +663,9 @@ cudaError_t launch_to_c64(const double2* in, float2* out, int64_t n_items, cudaS
     template cudaError_t launch_evolve<T>(const DevH&, int, int, bool, bool, double, double, double, \
                                           const ChainsT<T>&, cudaStream_t);                        \
     template cudaError_t launch_apply<T>(const DevH&, int, int, double, const vec2_t<T>*,           \
-                                         vec2_t<T>*, cudaStream_t);
+                                         vec2_t<T>*, cudaStream_t);                                  \
+    template cudaError_t launch_dot<T>(int64_t, int, const vec2_t<T>*, const vec2_t<T>*, double*, int, \
+                                       double2*, int64_t, cudaStream_t);
 
 KG_INSTANTIATE(double)
 KG_INSTANTIATE(float)

@@ -103,3 +103,13 @@ def test_gpu_entry_points_fail_loudly_without_a_device():
     with pytest.raises(kg.KgError) as e:
         kg.build_hamiltonian(ki.SHEET, 8, 8, emax_ev=8.505)
     assert e.value.status == -6
+
+
+def test_ftm_sum_matches_oracle():
+    rng = np.random.default_rng(5)
+    nm = 40
+    f = rng.normal(size=(2, 2 * nm + 1)) + 1j * rng.normal(size=(2, 2 * nm + 1))
+    en = post.energy_grid()
+    ref = post.ftm_density(f, en, 8.505, 77.7)
+    got = kg.ftm_sum(f, en, 8.505, 77.7)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))

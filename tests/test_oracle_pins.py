@@ -479,3 +479,43 @@ def test_mlp_oracle_gelu_and_layout():
     fd = (mlp.gelu(z + 1e-6) - mlp.gelu(z - 1e-6)) / 2e-6
     assert np.max(np.abs(fd - mlp.gelu_grad(z))) < 1e-8
     assert mlp.n_params() == 3 * 256 + 256 + 3 * (256 * 256 + 256) + 256 + 1 == 198657
+
+
+
+# ------------------------------------------------------------------ Fourier moments (FTM)
+
+def test_ftm_moments_match_exact_diagonalisation():
+    """Algorithm 4: F_n = <L|U(n dtau)|R> = sum_k conj(L_k) R_k exp(-i pi n e_k) for the
+    scaled step dtau -> pi (Sec. 4.2), n = -N_m..N_m."""
+    for w in _systems()[:3]:
+        h = oracle.from_workload(w)
+        ed = _ED(h)
+        l = _vec(h.n, 1, w.vacancies)
+        r = _vec(h.n, 2, w.vacancies) * (1 + 0.3j)
+        f = oracle.ftm_moments(h, l, r, 12)
+        a, b = ed.v.T @ l, ed.v.T @ r
+        n = np.arange(-12, 13)
+        ref = np.exp(-1j * np.pi * np.outer(n, ed.e)) @ (np.conj(a) * b)
+        assert _rel(f, ref) < 1e-12
+
+
+def test_ftm_dos_integrates_to_state_count():
+    """Eq. (22) with the Hanning window (Eq. 28, w_0 = 1): int rho dE over
+    [-E_max, E_max] = 2 F_0 / Omega, and FTM agrees with KPM on integrated windows
+    (both are approximations of the same delta function, Sec. 4.2)."""
+    w = ki.sheet_cells(12, 12, vacancy_conc=0.02, lattice_seed=3)
+    h = oracle.from_workload(w)
+    phi = _vec(h.n, 5, w.vacancies)
+    f = oracle.ftm_moments(h, phi, phi, 60)
+    en = np.linspace(-h.emax_ev, h.emax_ev, 4001)
+    rho = post.ftm_density(f, en, h.emax_ev, h.area_nm2)
+    integral = np.trapezoid(rho, en)
+    assert abs(integral / (2 * f[60].real / h.area_nm2) - 1) < 1e-3
+    mu = oracle.kpm_moments(h, phi, phi, 200)
+    en2 = np.linspace(-8.0, 8.0, 1601)
+    rk = post.kpm_density(mu, en2, h.emax_ev, h.area_nm2)
+    rf = post.ftm_density(f, en2, h.emax_ev, h.area_nm2)
+    for lo, hi in [(-8, -4), (-4, -1), (-1, 1), (1, 4), (4, 8)]:
+        sel = (en2 >= lo) & (en2 <= hi)
+        ik, iff = np.trapezoid(rk[sel], en2[sel]), np.trapezoid(rf[sel], en2[sel])
+        assert abs(ik - iff) < 0.05 * max(abs(ik), 1e-3 * integral), (lo, hi, ik, iff)
