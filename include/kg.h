@@ -326,6 +326,29 @@ kg_status kg_ftm_sum(const double* f, int n_sets, int n_m, const double* energie
 kg_status kg_conductivity(int formula, const double* density, int n_times, int n_e,
                           double dt_fs, double* out);
 
+/* Ballistic regime (Sec. 5.1): DX^2 = (rho DX^2) / rho (Eq. 10), length L = 2 sqrt(DX^2)
+ * (Eq. 50) in nm and conductance G = (W / L) sigma^E1 (Eq. 51) in e^2/h, with sigma^E1 from
+ * Eq. 9.  rho: host [n_e] (1/(eV nm^2)); rho_dx2: host [N_c][n_e] (1/eV); width_nm: the
+ * sample width W across the transport direction; outputs host [N_c][n_e]; 0 where L = 0. */
+kg_status kg_ballistic(const double* rho, const double* rho_dx2, int n_times, int n_e, double dt_fs,
+                       double width_nm, double* length_out, double* g_out);
+
+/* Semi-classical conductivity (Sec. 5.2): max_out[e] = max_{t > 0} sigma(E, t) (Eq. 53);
+ * avg_out[e] = (1/(t2 - t1)) int_{t1}^{t2} sigma(E, t) dt (Eq. 54), trapezoid over the grid
+ * times t_m = m dt_fs inside [t1, t2].  sigma: host [N_c][n_e]; either output may be NULL. */
+kg_status kg_sigma_sc(const double* sigma, int n_times, int n_e, double dt_fs, double t1_fs,
+                      double t2_fs, double* max_out, double* avg_out);
+
+/* Pade [m/n] fit of a late-time MSD (Sec. 5.3, Eq. 58), y(t) = sum_{j=0}^{m} a_j t^j /
+ * (1 + sum_{k=1}^{n} b_k t^k) (the printed denominator sum from k = 0 is read as k = 1),
+ * by linear least squares on y (1 + sum b_k t^k) = sum a_j t^j.  coef_out: host
+ * [m + 1 + n] = (a_0..a_m, b_1..b_n).  KG_EINVAL when n_points < m + 1 + n. */
+kg_status kg_pade_fit(const double* t, const double* y, int n_points, int m, int n, double* coef_out);
+
+/* Value and derivative d/dt of the fitted approximant (for sigma^E1 = e^2 rho d(DX^2)/(2 dt)). */
+kg_status kg_pade_eval(const double* coef, int m, int n, const double* t, int n_points,
+                       double* value_out, double* deriv_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,3 +86,44 @@ def ftm_density(f, energies_ev, emax_ev: float, area_nm2: float) -> np.ndarray:
     e = np.asarray(energies_ev) / emax_ev
     phase = np.exp(1j * np.pi * np.outer(e, n))
     return np.real(phase @ (w * f).T).T / (emax_ev * area_nm2)
+
+
+def ballistic(rho, rho_dx2, t_fs, width_nm: float):
+    """Eqs. (50)-(51): DX^2 = rho DX^2 / rho, L = 2 sqrt(DX^2), G = (W / L) sigma^E1."""
+    dx2 = np.where(np.asarray(rho)[None, :] > 0, rho_dx2 / np.asarray(rho)[None, :], 0.0)
+    length = 2.0 * np.sqrt(np.maximum(dx2, 0.0))
+    s1 = sigma_e1(rho_dx2, t_fs)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        g = np.where(length > 0, width_nm / length * s1, 0.0)
+    return length, g
+
+
+def sigma_sc_max(sigma):
+    """Eq. (53): maximum over the correlation times t > 0."""
+    return np.max(np.asarray(sigma)[1:], axis=0)
+
+
+def sigma_sc_average(sigma, t_fs, t1: float, t2: float):
+    """Eq. (54): (1/(t2 - t1)) int_{t1}^{t2} sigma dt, trapezoid on the grid points in [t1, t2]."""
+    t = np.asarray(t_fs)
+    sel = (t >= t1 - 1e-9) & (t <= t2 + 1e-9)
+    return np.trapezoid(np.asarray(sigma)[sel], t[sel], axis=0) / (t[sel][-1] - t[sel][0])
+
+
+def pade_fit(t, y, m: int = 2, n: int = 2):
+    """Eq. (58) with the denominator sum from k = 1: least squares (numpy.linalg.lstsq) on
+    sum_j a_j t^j - y sum_k b_k t^k = y."""
+    t = np.asarray(t, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    cols = [t ** j for j in range(m + 1)] + [-y * t ** k for k in range(1, n + 1)]
+    a = np.stack(cols, axis=1)
+    s = np.linalg.norm(a, axis=0)
+    x = np.linalg.lstsq(a / s, y, rcond=None)[0]
+    return x / s
+
+
+def pade_value(coef, t, m: int = 2, n: int = 2):
+    t = np.asarray(t, dtype=np.float64)
+    num = sum(coef[j] * t ** j for j in range(m + 1))
+    den = 1.0 + sum(coef[m + k] * t ** k for k in range(1, n + 1))
+    return num / den

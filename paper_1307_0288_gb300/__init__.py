@@ -83,6 +83,10 @@ ABI = [
     ("kg_batched_test_stall", _I, [_I]),
     ("kg_ftm_dos_moments", _I, [_P, ctypes.POINTER(_Run), _P, _P]),
     ("kg_ftm_sum", _I, [_P, _I, _I, _P, _I, _D, _D, _P]),
+    ("kg_ballistic", _I, [_P, _P, _I, _I, _D, _D, _P, _P]),
+    ("kg_sigma_sc", _I, [_P, _I, _I, _D, _D, _D, _P, _P]),
+    ("kg_pade_fit", _I, [_P, _P, _I, _I, _I, _P]),
+    ("kg_pade_eval", _I, [_P, _I, _I, _P, _I, _P, _P]),
     ("kg_mlp_create", _I, [_P, _P, ctypes.POINTER(_P)]),
     ("kg_mlp_destroy", None, [_P]),
     ("kg_mlp_get_params", _I, [_P, _P]),
@@ -516,3 +520,43 @@ def conductivity(formula: int, density, dt_fs: float) -> np.ndarray:
     _check(lib().kg_conductivity(int(formula), d.ctypes.data, d.shape[0], d.shape[1],
                                  float(dt_fs), out.ctypes.data))
     return out
+
+
+def ballistic(rho, rho_dx2, dt_fs: float, width_nm: float):
+    """kg_ballistic -> (L [N_c][n_E] nm, G [N_c][n_E] e^2/h)  (Eqs. 50-51)."""
+    r = np.ascontiguousarray(rho, dtype=np.float64)
+    d = np.ascontiguousarray(rho_dx2, dtype=np.float64)
+    length = np.zeros_like(d)
+    g = np.zeros_like(d)
+    _check(lib().kg_ballistic(r.ctypes.data, d.ctypes.data, d.shape[0], d.shape[1], float(dt_fs),
+                              float(width_nm), length.ctypes.data, g.ctypes.data))
+    return length, g
+
+
+def sigma_sc(sigma, dt_fs: float, t1_fs: float, t2_fs: float):
+    """kg_sigma_sc -> (max over t > 0 [n_E], block average over [t1, t2] [n_E])  (Eqs. 53-54)."""
+    s = np.ascontiguousarray(sigma, dtype=np.float64)
+    mx = np.zeros(s.shape[1])
+    av = np.zeros(s.shape[1])
+    _check(lib().kg_sigma_sc(s.ctypes.data, s.shape[0], s.shape[1], float(dt_fs), float(t1_fs), float(t2_fs),
+                             mx.ctypes.data, av.ctypes.data))
+    return mx, av
+
+
+def pade_fit(t, y, m: int = 2, n: int = 2) -> np.ndarray:
+    """kg_pade_fit -> (a_0..a_m, b_1..b_n)  (Eq. 58)."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    c = np.zeros(m + 1 + n)
+    _check(lib().kg_pade_fit(t.ctypes.data, y.ctypes.data, len(t), m, n, c.ctypes.data))
+    return c
+
+
+def pade_eval(coef, t, m: int = 2, n: int = 2):
+    """kg_pade_eval -> (value, derivative) of the fitted approximant at t."""
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    v = np.zeros(len(t))
+    d = np.zeros(len(t))
+    _check(lib().kg_pade_eval(c.ctypes.data, m, n, t.ctypes.data, len(t), v.ctypes.data, d.ctypes.data))
+    return v, d

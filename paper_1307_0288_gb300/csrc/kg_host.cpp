@@ -1,6 +1,7 @@
 // Host-side parts of the library: error reporting, the lattice/neighbour table,
 // Bessel coefficients, Jackson damping, the Chebyshev energy sums and the running
 // conductivities.  None of this needs a GPU.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -251,6 +252,124 @@ kg_status kg_ftm_sum(const double* f, int n_sets, int n_m, const double* energie
             }
             out[(size_t)s * n_e + e] = acc / (emax_ev * area_nm2);
         }
+    }
+    return KG_OK;
+}
+
+// Ballistic length and conductance (Eqs. 50-51): DX^2 = (rho DX^2) / rho (Eq. 10),
+// L = 2 sqrt(DX^2), G = (W / L) sigma^E1, sigma^E1 from Eq. 9 (central differences).
+kg_status kg_ballistic(const double* rho, const double* rho_dx2, int n_times, int n_e, double dt_fs,
+                       double width_nm, double* length_out, double* g_out) {
+    if (!rho || !rho_dx2 || !length_out || !g_out || n_times < 2 || n_e < 1 || !(dt_fs > 0) || !(width_nm > 0))
+        return fail(KG_EINVAL, "kg_ballistic: bad arguments");
+    std::vector<double> s1((size_t)n_times * n_e);
+    KG_TRY(kg_conductivity(KG_SIGMA_E1, rho_dx2, n_times, n_e, dt_fs, s1.data()));
+    for (int t = 0; t < n_times; t++)
+        for (int e = 0; e < n_e; e++) {
+            const size_t k = (size_t)t * n_e + e;
+            const double dx2 = rho[e] > 0 ? rho_dx2[k] / rho[e] : 0.0;
+            const double len = dx2 > 0 ? 2.0 * std::sqrt(dx2) : 0.0;
+            length_out[k] = len;
+            g_out[k] = len > 0 ? width_nm / len * s1[k] : 0.0;
+        }
+    return KG_OK;
+}
+
+// Semi-classical conductivity (Sec. 5.2): the maximum over t > 0 (Eq. 53) and the average
+// over the block t1 <= t <= t2 (Eq. 54, trapezoid over the grid points in the block).
+kg_status kg_sigma_sc(const double* sigma, int n_times, int n_e, double dt_fs, double t1_fs, double t2_fs,
+                      double* max_out, double* avg_out) {
+    if (!sigma || n_times < 2 || n_e < 1 || !(dt_fs > 0) || !(t2_fs > t1_fs))
+        return fail(KG_EINVAL, "kg_sigma_sc: bad arguments");
+    const int k1 = std::max(0, (int)std::ceil(t1_fs / dt_fs - 1e-9));
+    const int k2 = std::min(n_times - 1, (int)std::floor(t2_fs / dt_fs + 1e-9));
+    if (avg_out && k2 <= k1) return fail(KG_EINVAL, "kg_sigma_sc: the block holds fewer than two times");
+    for (int e = 0; e < n_e; e++) {
+        if (max_out) {
+            double m = sigma[(size_t)1 * n_e + e];
+            for (int t = 2; t < n_times; t++) m = std::fmax(m, sigma[(size_t)t * n_e + e]);
+            max_out[e] = m;
+        }
+        if (avg_out) {
+            double acc = 0.0;
+            for (int t = k1; t < k2; t++)
+                acc += 0.5 * dt_fs * (sigma[(size_t)t * n_e + e] + sigma[(size_t)(t + 1) * n_e + e]);
+            avg_out[e] = acc / ((k2 - k1) * dt_fs);
+        }
+    }
+    return KG_OK;
+}
+
+// Pade [m/n] fit (Eq. 58; reading: the denominator sum starts at k = 1):
+//   y(t) = sum_{j<=m} a_j t^j / (1 + sum_{1<=k<=n} b_k t^k),
+// linearised as sum_j a_j t^j - y sum_k b_k t^k = y and solved in the least-squares sense
+// with Householder QR on the columns scaled to unit norm.  coef_out = (a_0..a_m, b_1..b_n).
+kg_status kg_pade_fit(const double* t, const double* y, int n_points, int m, int n, double* coef_out) {
+    const int p = m + 1 + n;
+    if (!t || !y || !coef_out || m < 0 || n < 0 || n_points < p) return fail(KG_EINVAL, "kg_pade_fit: bad arguments");
+    std::vector<double> A((size_t)n_points * p), b(y, y + n_points), scale(p, 0.0);
+    for (int i = 0; i < n_points; i++) {
+        double tp = 1.0;
+        for (int j = 0; j <= m; j++, tp *= t[i]) A[(size_t)i * p + j] = tp;
+        tp = t[i];
+        for (int k = 1; k <= n; k++, tp *= t[i]) A[(size_t)i * p + m + k] = -y[i] * tp;
+    }
+    for (int c = 0; c < p; c++) {
+        double s = 0.0;
+        for (int i = 0; i < n_points; i++) s += A[(size_t)i * p + c] * A[(size_t)i * p + c];
+        scale[c] = s > 0 ? std::sqrt(s) : 1.0;
+        for (int i = 0; i < n_points; i++) A[(size_t)i * p + c] /= scale[c];
+    }
+    // Householder QR: A = Q R, then R x = Q^T b
+    for (int c = 0; c < p; c++) {
+        double norm = 0.0;
+        for (int i = c; i < n_points; i++) norm += A[(size_t)i * p + c] * A[(size_t)i * p + c];
+        norm = std::sqrt(norm);
+        if (norm == 0.0) return fail(KG_EINVAL, "kg_pade_fit: rank-deficient system");
+        const double alpha = A[(size_t)c * p + c] > 0 ? -norm : norm;
+        std::vector<double> v(n_points - c);
+        for (int i = c; i < n_points; i++) v[i - c] = A[(size_t)i * p + c];
+        v[0] -= alpha;
+        double vv = 0.0;
+        for (double q : v) vv += q * q;
+        if (vv == 0.0) continue;
+        for (int cc = c; cc < p; cc++) {
+            double d = 0.0;
+            for (int i = c; i < n_points; i++) d += v[i - c] * A[(size_t)i * p + cc];
+            d = 2.0 * d / vv;
+            for (int i = c; i < n_points; i++) A[(size_t)i * p + cc] -= d * v[i - c];
+        }
+        double d = 0.0;
+        for (int i = c; i < n_points; i++) d += v[i - c] * b[i];
+        d = 2.0 * d / vv;
+        for (int i = c; i < n_points; i++) b[i] -= d * v[i - c];
+    }
+    for (int c = p - 1; c >= 0; c--) {
+        double s = b[c];
+        for (int cc = c + 1; cc < p; cc++) s -= A[(size_t)c * p + cc] * coef_out[cc];
+        coef_out[c] = s / A[(size_t)c * p + c];
+    }
+    for (int c = 0; c < p; c++) coef_out[c] /= scale[c];
+    return KG_OK;
+}
+
+// Value and t-derivative of the fitted Pade approximant at n_points times.
+kg_status kg_pade_eval(const double* coef, int m, int n, const double* t, int n_points, double* value_out,
+                       double* deriv_out) {
+    if (!coef || !t || m < 0 || n < 0 || n_points < 1) return fail(KG_EINVAL, "kg_pade_eval: bad arguments");
+    for (int i = 0; i < n_points; i++) {
+        double num = 0.0, dnum = 0.0, den = 1.0, dden = 0.0, tp = 1.0;
+        for (int j = 0; j <= m; j++, tp *= t[i]) {
+            num += coef[j] * tp;
+            if (j > 0) dnum += j * coef[j] * tp / t[i];
+        }
+        tp = t[i];
+        for (int k = 1; k <= n; k++, tp *= t[i]) {
+            den += coef[m + k] * tp;
+            dden += k * coef[m + k] * tp / t[i];
+        }
+        if (value_out) value_out[i] = num / den;
+        if (deriv_out) deriv_out[i] = (dnum * den - num * dden) / (den * den);
     }
     return KG_OK;
 }

@@ -113,3 +113,26 @@ def test_ftm_sum_matches_oracle():
     ref = post.ftm_density(f, en, 8.505, 77.7)
     got = kg.ftm_sum(f, en, 8.505, 77.7)
     assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_ballistic_sigma_sc_and_pade_match_oracle():
+    rng = np.random.default_rng(9)
+    t = post.time_grid(16, 2.0)
+    rho = rng.uniform(0.01, 0.1, size=7)
+    rdx = np.cumsum(rng.uniform(0, 1, size=(16, 7)), axis=0) * rho
+    rdx[0] = 0
+    l1, g1 = kg.ballistic(rho, rdx, t[1], 9.0)
+    l2, g2 = post.ballistic(rho, rdx, t, 9.0)
+    assert np.allclose(l1, l2, rtol=1e-13) and np.allclose(g1, g2, rtol=1e-12, atol=1e-14)
+    sig = rng.normal(size=(16, 7))
+    mx, av = kg.sigma_sc(sig, t[1], t[3], t[12])
+    assert np.allclose(mx, post.sigma_sc_max(sig))
+    assert np.allclose(av, post.sigma_sc_average(sig, t, t[3], t[12]), rtol=1e-12)
+    tt = np.linspace(1.0, 300.0, 80)
+    y = 40 * tt / (1 + 0.05 * tt) + rng.normal(scale=0.05, size=80)
+    c1 = kg.pade_fit(tt, y)
+    c2 = post.pade_fit(tt, y)
+    v1, d1 = kg.pade_eval(c1, tt)
+    assert np.allclose(v1, post.pade_value(c2, tt), rtol=1e-6)
+    fd = (post.pade_value(c1, tt + 1e-4) - post.pade_value(c1, tt - 1e-4)) / 2e-4
+    assert np.allclose(d1, fd, rtol=1e-5)

@@ -519,3 +519,39 @@ def test_ftm_dos_integrates_to_state_count():
         sel = (en2 >= lo) & (en2 <= hi)
         ik, iff = np.trapezoid(rk[sel], en2[sel]), np.trapezoid(rf[sel], en2[sel])
         assert abs(ik - iff) < 0.05 * max(abs(ik), 1e-3 * integral), (lo, hi, ik, iff)
+
+
+# ------------------------------------------------------------------ ballistic, sigma_sc, Pade
+
+def test_ballistic_conductance_forms_agree_when_msd_is_quadratic():
+    """Sec. 5.1: with DX^2 = v^2 t^2, L = 2 v t (Eq. 50) and G = (W/L) sigma^E1 (Eq. 51)
+    equals (W/2) e^2 rho sqrt(v^2) (Eq. 52), i.e. (W/2) h rho v in units of e^2/h."""
+    t = post.time_grid(9, 1.0)
+    rho = np.array([0.02, 0.05, 0.11])
+    v = np.array([0.3, 0.6, 0.9])
+    rdx = rho[None, :] * (v[None, :] * t[:, None]) ** 2
+    length, g = post.ballistic(rho, rdx, t, 12.0)
+    assert np.allclose(length[1:], 2 * v[None, :] * t[1:, None], rtol=1e-12)
+    ref = 0.5 * 12.0 * post.H_EV_FS * rho * v
+    assert np.allclose(g[1:-1], ref[None, :], rtol=1e-12)
+
+
+def test_sigma_sc_definitions():
+    """Eq. (53) maximum and Eq. (54) block average: a plateau gives its value for both;
+    a ramp sigma = c t averages to c (t1 + t2) / 2."""
+    t = post.time_grid(21, 1.0)
+    plateau = np.full((21, 3), 2.5)
+    plateau[0] = 0.0
+    assert np.allclose(post.sigma_sc_max(plateau), 2.5)
+    assert np.allclose(post.sigma_sc_average(plateau, t, t[4], t[15]), 2.5)
+    ramp = np.outer(t, [1.0, 2.0])
+    assert np.allclose(post.sigma_sc_average(ramp, t, t[2], t[10]), [1.0, 2.0] * (t[2] + t[10]) / 2)
+
+
+def test_pade_fit_recovers_a_rational_function():
+    """Eq. (58) [2/2]: data drawn from a known approximant are fitted back exactly."""
+    t = np.linspace(1.0, 200.0, 60)
+    coef = np.array([0.5, 3.0, 0.02, 0.01, 2e-4])
+    y = post.pade_value(coef, t)
+    got = post.pade_fit(t, y)
+    assert np.allclose(got, coef, rtol=1e-8)

@@ -288,3 +288,24 @@ def test_kpm_is_cheaper_than_ftm_at_equal_resolution():
         assert abs(np.trapezoid(rk[s], en[s]) - np.trapezoid(rf[s], en[s])) < 0.05 * total
     print(f"KPM M=1000: {t_kpm:.3f} s, FTM N_m=500: {t_ftm:.3f} s, FTM N_m=80 (equal resolution): {t_ftm_eq:.3f} s")
     assert t_ftm_eq > 3 * t_kpm
+
+
+def test_clean_zgnr_einstein_conductance_is_quantised():
+    """Sec. 5.1 / Fig. 4: a clean zigzag ribbon (8 chains, 8192 cells, 131,072 sites) in the
+    ballistic regime.  Where the Bloch bands give one mode (|E| < 1.32 eV), G = (W/L)
+    sigma^E1 = 2 e^2/h (spin included); with three modes of different velocities the
+    Einstein estimate exceeds 6 e^2/h (sqrt<v^2> > <|v|>, the overshoot the paper discusses)."""
+    w = ki.zgnr(8, 8192, n_vec=16)
+    h = kg.from_workload(w)
+    phi = w.vectors(16)
+    m, nc, dt = 1200, 4, 4.0
+    dos = kg.dos_moments(h, phi, m).mean(axis=0)
+    msd = kg.msd(h, phi, m, nc, dt).mean(axis=0)
+    en = np.array([0.6, 0.8, 1.0, 1.7, 1.9])
+    rho = kg.kpm_sum(dos.real, en, h.emax_ev, h.area_nm2)
+    rdx = kg.kpm_sum(msd.real, en, h.emax_ev, h.area_nm2)
+    dt_fs = dt * kg.HBAR_EV_FS / 2.7
+    width = 1.5 * w.ny * w.bond_nm
+    _, g = kg.ballistic(rho, rdx, dt_fs, width)
+    assert np.allclose(g[2, :3], 2.0, rtol=0.05), g[2]
+    assert np.all(g[2, 3:] > 6.0 * 0.97) and np.all(g[2, 3:] < 6.0 * 1.6), g[2]
