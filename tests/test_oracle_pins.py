@@ -545,7 +545,7 @@ def test_sigma_sc_definitions():
     assert np.allclose(post.sigma_sc_max(plateau), 2.5)
     assert np.allclose(post.sigma_sc_average(plateau, t, t[4], t[15]), 2.5)
     ramp = np.outer(t, [1.0, 2.0])
-    assert np.allclose(post.sigma_sc_average(ramp, t, t[2], t[10]), [1.0, 2.0] * (t[2] + t[10]) / 2)
+    assert np.allclose(post.sigma_sc_average(ramp, t, t[2], t[10]), np.array([1.0, 2.0]) * (t[2] + t[10]) / 2)
 
 
 def test_pade_fit_recovers_a_rational_function():
