@@ -49,7 +49,10 @@ CELLS, VAC, R, M, DT, PREC = WORKLOADS[DEFAULT_WORKLOAD]
 METRIC = "Chebyshev site-updates/s and HBM GB/s vs peak; σ(E,t) time at 1e-5 err vs FP64"
 UNIT = "site-updates/s"
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (profiling recipe table); DFMA probe measured 1.20
-KPM_FLOPS_PER_SITE_STEP = 16   # algorithmic FP64 flops of one doubling-KPM site update
+# FP64 work of one doubling-KPM site-vector update on the DP pipe: the recursion
+# y = c (a + b + d) - z costs 3 FMA per real component, 6 FMA = 12 flops per complex item.
+# The two inner products per item are double-float sums on the FP32 pipe.
+KPM_FP64_FLOPS_PER_ITEM = 12
 CONFIG_NAME = DEFAULT_WORKLOAD
 
 
@@ -64,12 +67,17 @@ def paper_work_per_step(n_sites: int, n_vec: int, n_moments: int, n_p: int) -> f
     return float(n_sites) * n_vec * ((n_moments - 1) + 4 * (n_p - 1))
 
 
-def _profiled_traffic(kernel_file: str, profile: str):
+KPM_SOURCES = ("kg_kernels.cu", "kg_dot.cuh")
+
+
+def _profiled_traffic(kernel_files, profile: str):
     """DRAM bytes per launch from a committed ncu summary, or None when the kernel
-    source changed since the counters were taken."""
+    sources (hashed in the given order, concatenated) changed since the counters
+    were taken."""
     import hashlib
     try:
-        src = open(os.path.join(ROOT, "paper_1307_0288_gb300", "csrc", kernel_file), "rb").read()
+        src = b"".join(open(os.path.join(ROOT, "paper_1307_0288_gb300", "csrc", f), "rb").read()
+                       for f in kernel_files)
         text = open(os.path.join(ROOT, "profiles", profile)).read()
     except OSError:
         return None
@@ -304,7 +312,7 @@ def run_ours(args):
     value = work / (ms * 1e-3)
     executed = (cnt["kpm_site_steps"] + cnt["evolve_site_steps"]) * world / (ms * 1e-3)
     kpm_launch_ms = cnt["kpm_ms"] / max(cnt["kpm_launches"], 1)
-    flops_per_launch = KPM_FLOPS_PER_SITE_STEP * w.n_sites * R
+    flops_per_launch = KPM_FP64_FLOPS_PER_ITEM * w.n_sites * R
     achieved_tflops = flops_per_launch / (kpm_launch_ms * 1e-3) / 1e12
     vec_b = 16 if PREC == "f64" else 8
     bytes_per_launch = w.n_sites * (12 + 3 * vec_b * R)
@@ -313,10 +321,10 @@ def run_ours(args):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback"
     if PREC == "f64":
-        roofline = {"bound": "alu", "kernel": "kpm_sym_kernel<double> (FP64 doubling KPM step)",
+        roofline = {"bound": "alu", "kernel": "kpm_sym_kernel<double> (FP64 doubling KPM step, 6 DFMA per site-vector)",
                     "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved_tflops / FP64_PEAK_TFLOPS,
-                    "traffic": _profiled_traffic("kg_kernels.cu", "kpm_sym_kernel_msd_sheet_2M.md"),
+                    "traffic": _profiled_traffic(KPM_SOURCES, "kpm_sym_kernel_msd_sheet_2M.md"),
                     "algorithmic_bytes": bytes_per_launch,
                     "peak_source": "nominal FP64 of the profiling recipe (DFMA probe: 1.20)",
                     "avg_launch_ms": kpm_launch_ms,
@@ -326,7 +334,7 @@ def run_ours(args):
         roofline = {"bound": "hbm", "kernel": "kpm_sym_kernel<float> (complex64 doubling KPM step)",
                     "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_gbs / hbm_peak,
-                    "traffic": _profiled_traffic("kg_kernels.cu", "kpm_sym_kernel_c64_sheet_8M.md"),
+                    "traffic": _profiled_traffic(KPM_SOURCES, "kpm_sym_kernel_c64_sheet_8M.md"),
                     "algorithmic_bytes": bytes_per_launch, "peak_source": hbm_src,
                     "avg_launch_ms": kpm_launch_ms}
     if rank != 0:
@@ -410,7 +418,7 @@ def run_batched(args):
     work = float(n_sites) * rv * (mm - 1) * args.steps * world
     steps_per_call = (mm + 1) // 2
     step_ms = ms / args.steps / steps_per_call
-    flops = KPM_FLOPS_PER_SITE_STEP * n_sites * rv
+    flops = KPM_FP64_FLOPS_PER_ITEM * n_sites * rv
     achieved = flops / (step_ms * 1e-3) / 1e12
     bytes_step = n_sites * (12 + 48 * rv)
     peaks = _peaks()

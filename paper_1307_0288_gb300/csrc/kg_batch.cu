@@ -19,7 +19,8 @@
 // The block width RB (vectors one thread group covers per pass: 8, 16, 32 or 64) is
 // chosen by a measured autotuner; the device work of a call (flag reset, persistent
 // kernel, reduction) is captured once per (RB, step count) in a CUDA graph and
-// replayed.
+// replayed.  The recursion is FP64 (6 DFMA per site-vector); the moments' inner
+// products are double-float sums on the FP32 pipe (kg_dot.cuh).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,6 +31,7 @@
 #include <string>
 #include <vector>
 
+#include "kg_dot.cuh"
 #include "kg_internal.h"
 
 namespace kg {
@@ -131,9 +133,7 @@ __global__ void __launch_bounds__(kBThreads) batched_kpm_kernel(BatchArgs a) {
         double2* out = (n & 1) ? a.A : a.B;   // in place over phi_{n-1} from n = 1 on
         const double c = n == 0 ? h : 2.0 * h;
         const double ec = n == 0 ? 1.0 : 2.0;
-        double acc0[kChunks], acc1[kChunks];
-#pragma unroll
-        for (int q = 0; q < kChunks; q++) acc0[q] = acc1[q] = 0.0;
+        Dot64 acc0[kChunks], acc1[kChunks];
         for (int64_t site = s0 + sl; site < s1; site += kSitesPerPass) {
             const int32_t i0 = __ldg(a.idx + site), i1 = __ldg(a.idx + n_total + site),
                           i2 = __ldg(a.idx + 2 * n_total + site);
@@ -154,13 +154,15 @@ __global__ void __launch_bounds__(kBThreads) batched_kpm_kernel(BatchArgs a) {
                 const double yr = fma(c, va.x, fma(c, vb.x, fma(c, vc.x, tr)));
                 const double yi = fma(c, va.y, fma(c, vb.y, fma(c, vc.y, ti)));
                 __stcg(out + site * R + r, make_double2(yr, yi));
-                acc0[q] = fma(x.x, x.x, fma(x.y, x.y, acc0[q]));
-                acc1[q] = fma(yr, x.x, fma(yi, x.y, acc1[q]));
+                acc0[q].add_prod(x.x, x.x);
+                acc0[q].add_prod(x.y, x.y);
+                acc1[q].add_prod(yr, x.x);
+                acc1[q].add_prod(yi, x.y);
             }
         }
         double* dst = a.partial + ((int64_t)n * a.n_cta + cta) * R * 2;
 #pragma unroll
-        for (int q = 0; q < kChunks; q++) chunk_reduce<RB>(acc0[q], acc1[q], dst + q * RB * 2);
+        for (int q = 0; q < kChunks; q++) chunk_reduce<RB>(acc0[q].value(), acc1[q].value(), dst + q * RB * 2);
         // publish: all of this CTA's writes of step n before the flag
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -1,5 +1,6 @@
 // Kernels of the Chebyshev recursion for sm_103a, in two precisions:
-//   T = double: complex128 vectors, FP64 arithmetic and FP64 inner products;
+//   T = double: complex128 vectors, FP64 recursion, inner products in double-float
+//               arithmetic on the FP32 pipe (kg_dot.cuh), combined in FP64;
 //   T = float:  complex64 vectors, FP32 recursion, inner products accumulated per
 //               thread with exact FP32 products and compensated (TwoSum) sums, then
 //               combined across threads and blocks in FP64.
@@ -13,12 +14,14 @@
 // The GB300 executes FP64 at 1/64 of the FP32 rate (about 0.6e12 DFMA/s, and DADD
 // slower than DFMA), so the FP64 recursion is limited by the DP pipe, not by HBM.
 // FP64 operations are therefore all fused multiply-adds: the neighbour sum and the
-// "- T_{n-1}" fold into the hopping multiply (3 FMA per real component), and each
-// inner product costs 2 FMA per component.  The FP32 kernels are HBM-bound.
+// "- T_{n-1}" fold into the hopping multiply (3 FMA per real component), and the inner
+// products of the moments run on the FP32 and integer pipes (Acc<double> below), so a
+// site-vector update costs 6 DFMA.  The FP32 kernels are HBM-bound.
 #include <cuda_runtime.h>
 
 #include <unordered_map>
 
+#include "kg_dot.cuh"
 #include "kg_internal.h"
 
 namespace kg {
@@ -33,12 +36,9 @@ constexpr int kWarps = kThreads / 32;
 template <typename T>
 struct Acc;
 
+// FP64: double-float products and sums on the FP32 and integer pipes (kg_dot.cuh).
 template <>
-struct Acc<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
-    __device__ __forceinline__ double value() const { return s; }
-};
+struct Acc<double> : Dot64 {};
 
 // FP32 products are split exactly into p + e (e = fma(a, b, -p)); p is added with
 // Knuth's TwoSum, whose rounding error joins e in the compensation term c.  The
