@@ -70,10 +70,12 @@ def paper_work_per_step(n_sites: int, n_vec: int, n_moments: int, n_p: int) -> f
 KPM_SOURCES = ("kg_kernels.cu", "kg_dot.cuh")
 
 
-def _profiled_traffic(kernel_files, profile: str):
+def _profiled_traffic(kernel_files, profile: str, n_sites: int = 0):
     """DRAM bytes per launch from a committed ncu summary, or None when the kernel
     sources (hashed in the given order, concatenated) changed since the counters
-    were taken."""
+    were taken.  A summary captured on a smaller lattice states its
+    ``sites_per_launch:``; its traffic is scaled to ``n_sites`` (the step's traffic is
+    proportional to the site count at a fixed vector count)."""
     import hashlib
     try:
         src = b"".join(open(os.path.join(ROOT, "paper_1307_0288_gb300", "csrc", f), "rb").read()
@@ -83,11 +85,15 @@ def _profiled_traffic(kernel_files, profile: str):
         return None
     sha = hashlib.sha256(src).hexdigest()[:16]
     fields = dict(line.split(":", 1) for line in text.splitlines()
-                  if line.startswith(("kernel_source_sha256_16:", "traffic_bytes_per_launch:")))
+                  if line.startswith(("kernel_source_sha256_16:", "traffic_bytes_per_launch:",
+                                      "sites_per_launch:")))
     if fields.get("kernel_source_sha256_16", "").strip() != sha:
         return None
     try:
-        return int(fields["traffic_bytes_per_launch"].strip())
+        traffic = int(fields["traffic_bytes_per_launch"].strip())
+        if "sites_per_launch" in fields and n_sites:
+            traffic = int(round(traffic * n_sites / int(fields["sites_per_launch"].strip())))
+        return traffic
     except (KeyError, ValueError):
         return None
 
@@ -334,7 +340,7 @@ def run_ours(args):
         roofline = {"bound": "hbm", "kernel": "kpm_sym_kernel<float> (complex64 doubling KPM step)",
                     "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_gbs / hbm_peak,
-                    "traffic": _profiled_traffic(KPM_SOURCES, "kpm_sym_kernel_c64_sheet_8M.md"),
+                    "traffic": _profiled_traffic(KPM_SOURCES, "kpm_sym_kernel_c64_sheet_2M.md", w.n_sites),
                     "algorithmic_bytes": bytes_per_launch, "peak_source": hbm_src,
                     "avg_launch_ms": kpm_launch_ms}
     if rank != 0:

@@ -113,8 +113,19 @@ kg_status kg_lattice_neighbors(const kg_lattice* lattice, const int64_t* vacanci
 /* Moments and time evolution on the GPU                                      */
 /* ------------------------------------------------------------------------- */
 
-#define KG_FP64 0   /* complex128 vectors, FP64 arithmetic and moment sums */
+#define KG_FP64 0   /* complex128 vectors, FP64 recursion; moment sums see below */
 #define KG_C64 1    /* complex64 vectors, FP32 recursion, compensated sums combined in FP64 */
+
+/* Precision of the moments.  KG_FP64 runs the Chebyshev recursion and the time evolution
+ * in FP64; the inner products of the moments are formed in double-float arithmetic on
+ * the FP32 pipe (each FP64 factor split exactly into a float head and tail, products by
+ * FMA TwoProduct, per-thread TwoSum/FastTwoSum pairs) and combined across threads and
+ * blocks in FP64, about 2^-45 relative per term.  This holds for vector entries of
+ * magnitude in [2^-63, 2^63) (random-phase vectors and their Chebyshev iterates are
+ * O(1)); smaller entries contribute less accurately (nothing below 2^-126), and larger
+ * ones overflow.  Every entry point that returns moments checks them and fails with
+ * KG_ENUMERIC when one is NaN or infinite (NaN/Inf inputs, or entries >= 2^63), except
+ * kg_dos_moments_noalloc, which runs asynchronously and does not check. */
 
 typedef struct {
     int32_t n_moments;   /* M >= 1: moments C_0 .. C_{M-1} (Eqs. 32-34) */
@@ -183,7 +194,8 @@ kg_status kg_evolve(kg_hamiltonian* h, double dt, int which, double bessel_tol,
  *   run      n_moments M, n_vectors R (power of two <= 64), precision KG_FP64.
  *   phis     n_h pointers, host or device, member i's vectors [N_i][R][2].
  *   mu_out   host or device [n_h][R][M][2].
- * KG_ETIMEOUT if a CTA's wait for its neighbours gave up (the context stays usable). */
+ * KG_ETIMEOUT if a CTA's wait for its neighbours gave up (the context stays usable);
+ * KG_ENUMERIC if a moment is not finite. */
 kg_status kg_batched_dos_moments(kg_hamiltonian* const* hs, int n_h, const kg_run* run,
                                  const double* const* phis, double* mu_out);
 

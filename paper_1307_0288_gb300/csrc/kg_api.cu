@@ -55,7 +55,7 @@ struct kg_hamiltonian {
     // workspace
     static constexpr int kNumVec = 10;
     kg::DevBuf vec[kNumVec];
-    kg::DevBuf part_first, part_ring, moments;
+    kg::DevBuf part_first, part_ring, moments, flag;
     // timing
     bool timing = false;
     std::vector<kg::TimedPhase> phases;
@@ -152,6 +152,22 @@ static kg_status copy_out(kg_hamiltonian* h, const void* src, double* dst, size_
                                 is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                 h->stream));
     KG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return KG_OK;
+}
+
+// KG_ENUMERIC when a result on the device is not finite: non-finite input entries, or
+// FP64 vector entries beyond the range of the double-float inner products (2^63).
+static kg_status check_finite(kg_hamiltonian* h, const void* dev, size_t n_doubles) {
+    KG_TRY(h->flag.ensure(sizeof(int), h->stream));
+    KG_CUDA_TRY(cudaMemsetAsync(h->flag.p, 0, sizeof(int), h->stream));
+    KG_CUDA_TRY(launch_nonfinite((const double*)dev, (int64_t)n_doubles, (int*)h->flag.p, h->stream));
+    h->counters.other_launches += 1;
+    int bad = 0;
+    KG_CUDA_TRY(cudaMemcpyAsync(&bad, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    KG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (bad)
+        return fail(KG_ENUMERIC, "non-finite moments: the input vectors hold NaN/Inf entries or FP64 entries "
+                                 "of magnitude 2^63 or more");
     return KG_OK;
 }
 
@@ -531,6 +547,7 @@ void kg_destroy_hamiltonian(kg_hamiltonian* h) {
     h->part_first.release();
     h->part_ring.release();
     h->moments.release();
+    h->flag.release();
     for (auto& p : h->phases) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -548,6 +565,7 @@ kg_status kg_dos_moments(kg_hamiltonian* h, const kg_run* run, const double* phi
     KG_TRY(ensure_moments(h, (size_t)R * M));
     if (run->precision == KG_C64) KG_TRY(dos_impl<float>(h, R, M, phi));
     else KG_TRY(dos_impl<double>(h, R, M, phi));
+    KG_TRY(check_finite(h, h->moments.p, (size_t)R * M * 2));
     return copy_out(h, h->moments.p, mu_out, (size_t)R * M * sizeof(double2));
 }
 
@@ -562,6 +580,7 @@ kg_status kg_vac(kg_hamiltonian* h, const kg_run* run, const double* phi, double
     KG_TRY(ensure_moments(h, (size_t)R * NC * M));
     if (run->precision == KG_C64) KG_TRY(vac_impl<float>(h, R, M, NC, ser, phi));
     else KG_TRY(vac_impl<double>(h, R, M, NC, ser, phi));
+    KG_TRY(check_finite(h, h->moments.p, (size_t)R * NC * M * 2));
     return copy_out(h, h->moments.p, mu_out, (size_t)R * NC * M * sizeof(double2));
 }
 
@@ -576,6 +595,7 @@ kg_status kg_msd(kg_hamiltonian* h, const kg_run* run, const double* phi, double
     KG_TRY(ensure_moments(h, (size_t)R * NC * M));
     if (run->precision == KG_C64) KG_TRY(msd_impl<float>(h, R, M, NC, ser, phi));
     else KG_TRY(msd_impl<double>(h, R, M, NC, ser, phi));
+    KG_TRY(check_finite(h, h->moments.p, (size_t)R * NC * M * 2));
     return copy_out(h, h->moments.p, mu_out, (size_t)R * NC * M * sizeof(double2));
 }
 
@@ -617,6 +637,7 @@ kg_status kg_ftm_dos_moments(kg_hamiltonian* h, const kg_run* run, const double*
             h->counters.other_launches += 2;
         }
     }
+    KG_TRY(check_finite(h, mu, (size_t)R * width * 2));
     return copy_out(h, mu, f_out, (size_t)R * width * sizeof(double2));
 }
 

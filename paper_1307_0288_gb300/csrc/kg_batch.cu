@@ -134,9 +134,22 @@ __global__ void __launch_bounds__(kBThreads) batched_kpm_kernel(BatchArgs a) {
         const double c = n == 0 ? h : 2.0 * h;
         const double ec = n == 0 ? 1.0 : 2.0;
         Dot64 acc0[kChunks], acc1[kChunks];
-        for (int64_t site = s0 + sl; site < s1; site += kSitesPerPass) {
-            const int32_t i0 = __ldg(a.idx + site), i1 = __ldg(a.idx + n_total + site),
-                          i2 = __ldg(a.idx + 2 * n_total + site);
+        // neighbour indices of the next site are loaded one iteration ahead
+        int64_t site = s0 + sl;
+        int32_t j0 = 0, j1 = 0, j2 = 0;
+        if (site < s1) {
+            j0 = __ldg(a.idx + site);
+            j1 = __ldg(a.idx + n_total + site);
+            j2 = __ldg(a.idx + 2 * n_total + site);
+        }
+        for (; site < s1; site += kSitesPerPass) {
+            const int32_t i0 = j0, i1 = j1, i2 = j2;
+            const int64_t nxt = site + kSitesPerPass;
+            if (nxt < s1) {
+                j0 = __ldg(a.idx + nxt);
+                j1 = __ldg(a.idx + n_total + nxt);
+                j2 = __ldg(a.idx + 2 * n_total + nxt);
+            }
             double e = 0.0;
             if constexpr (ONSITE) e = ec * __ldg(a.onsite + site);
 #pragma unroll
@@ -664,9 +677,16 @@ kg_status kg_batched_dos_moments(kg_hamiltonian* const* hs, int n_h, const kg_ru
     KG_CUDA_TRY(cudaMemsetAsync(b->B + b->n_total * R, 0, (size_t)R * sizeof(double2), b->stream));
     KG_TRY(run_graph(b, b->tuned_rb, M));
     KG_TRY(check_error_flag(b));
+    // error[1]: non-finite moments (cleared with the wait flags by every graph replay)
+    KG_CUDA_TRY(launch_nonfinite((const double*)b->mu, (int64_t)n_h * R * M * 2, b->error + 1, b->stream));
+    int bad = 0;
+    KG_CUDA_TRY(cudaMemcpyAsync(&bad, b->error + 1, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     KG_CUDA_TRY(cudaMemcpyAsync(mu_out, b->mu, (size_t)n_h * R * M * sizeof(double2), cudaMemcpyDefault,
                                 b->stream));
     KG_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    if (bad)
+        return fail(KG_ENUMERIC, "batched: non-finite moments (input vectors with NaN/Inf entries or entries "
+                                 "of magnitude 2^63 or more)");
     return KG_OK;
 }
 

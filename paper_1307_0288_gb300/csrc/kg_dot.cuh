@@ -4,21 +4,22 @@
 // limited by the DP pipe.  The recursion itself stays in FP64 (6 DFMA per complex
 // site-vector update); the moments' inner products, which would cost another 4 DFMA,
 // are formed here in double-float arithmetic instead:
-//   * each FP64 factor x is split exactly by integer bit operations (no DP instruction)
-//     into a float head h (the top 24 significand bits, truncated) and a float tail l
-//     (the remaining 29 bits, rounded to 24), so |x - h - l| <= 2^-47 |x|;
+//   * each FP64 factor x is split by integer bit operations (no DP instruction, no
+//     conversion) into a float head h (the top 24 significand bits) and a float tail l
+//     (the next 23 bits), so |x - h - l| < 2^-46 |x|.  The tail is formed exactly as
+//     (2^p (1 + m 2^-23)) - 2^p with its 23 bits m placed in a float's mantissa;
 //   * a product a b is the exact TwoProduct of the heads, p + e with e = fma(ah, bh, -p)
 //     (Dekker's splitting replaced by the FMA), plus the cross terms ah bl + al bh in
 //     FP32; al bl (< 2^-46 |a b|) is dropped;
 //   * the per-thread sum is a double-float pair (s, c): Knuth's TwoSum adds p to s, its
 //     rounding error and the low part of the product join c, and FastTwoSum renormalises
 //     the pair after every term, so |c| stays below one unit in the last place of s.
-// Each term is accurate to about 2^-46 relative, and the per-thread sum to about
+// Each term is accurate to about 2^-45 relative, and the per-thread sum to about
 // k 2^-48 of the sum of |terms| after k terms; the pair is handed to the FP64 block
-// reduction as s + c.  Range: factors of magnitude in [2^-74, 2^63) and zero are
+// reduction as s + c.  Range: factors of magnitude in [2^-63, 2^63) and zero are
 // handled at that accuracy (the Chebyshev vectors of random-phase inputs are O(1));
-// smaller factors lose their tail, factors below 2^-126 count as 0, and non-finite or
-// huge factors give non-finite sums.  The explicit-rounding intrinsics keep the
+// smaller factors lose their tail below 2^-103 and count as 0 below 2^-126, and
+// non-finite or huge factors give non-finite sums.  The explicit-rounding intrinsics keep the
 // compiler from contracting or reassociating the compensated steps.
 #pragma once
 
@@ -34,9 +35,12 @@ __device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
     const int eh = min(ed - 896, 255);                    // biased float exponent of the head
     const unsigned mh = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
     hi = eh >= 1 ? __uint_as_float(sign | ((unsigned)eh << 23) | mh) : 0.0f;
-    const int es = min(ed - 948, 254);                    // biased float exponent of 2^(e - 52)
-    const float scale = es >= 1 ? __uint_as_float((unsigned)es << 23) : 0.0f;
-    const float t = __fmul_rn(__uint2float_rn(lw & 0x1FFFFFFFu), scale);
+    // tail bits 28..6 of the low word, weight 2^(e - 46) for bit 6: as 2^p (1 + m 2^-23) - 2^p
+    // with p = e - 23, i.e. biased float exponent ed - 919
+    const int et = min(ed - 919, 254);
+    const unsigned eb = et >= 1 ? (unsigned)et << 23 : 0u;
+    const float t = et >= 1 ? __fsub_rn(__uint_as_float(eb | ((lw & 0x1FFFFFFFu) >> 6)), __uint_as_float(eb))
+                            : 0.0f;
     lo = __uint_as_float(__float_as_uint(t) | sign);
 }
 

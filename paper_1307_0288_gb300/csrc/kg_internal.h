@@ -156,4 +156,8 @@ cudaError_t launch_to_c64(const double2* in, float2* out, int64_t n_items, cudaS
 // Grid size (CTAs) for a streaming kernel over n_items = n * R complex items.
 int stream_grid(int64_t n_items);
 
+// Sets *flag (device int, cleared by the caller) when one of the n doubles at p is
+// NaN or infinite; one kernel launch on stream s.
+cudaError_t launch_nonfinite(const double* p, int64_t n, int* flag, cudaStream_t s);
+
 }  // namespace kg

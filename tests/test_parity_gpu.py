@@ -228,6 +228,34 @@ def test_invalid_runs_are_rejected():
         kg.dos_moments(h, w.vectors(1), 0)
 
 
+def test_fp64_moment_range_and_non_finite_results():
+    """The FP64 path forms its inner products in double-float arithmetic: vector entries
+    scaled by 2^40 or 2^-40 still give the oracle's moments at 1e-10 (the moments scale
+    exactly by 2^80 / 2^-80); NaN entries or entries of 2^70 fail with KG_ENUMERIC."""
+    w = _systems()[1]
+    h = kg.from_workload(w)
+    ho = oracle.from_workload(w)
+    phi = w.vectors(2)
+    want = np.stack([oracle.kpm_moments(ho, phi[:, r], phi[:, r], 300) for r in range(2)])
+    for e in (40, -40):
+        got = kg.dos_moments(h, phi * 2.0 ** e, 300) * 2.0 ** (-2 * e)
+        assert _rel_per_vector(got, want) < TOL_MOMENTS, e
+        got = kg.vac(h, phi * 2.0 ** e, 64, 3, 1.0) * 2.0 ** (-2 * e)
+        ref = oracle.vac_moments(ho, phi[:, 0], 64, 3, 1.0)
+        assert _rel(got[0], ref) < TOL_MOMENTS, e
+    bad = phi.copy()
+    bad[5, 1] = np.nan
+    for x in (bad, phi * 2.0 ** 70):
+        with pytest.raises(kg.KgError) as err:
+            kg.dos_moments(h, x, 50)
+        assert err.value.status == -5
+        with pytest.raises(kg.KgError) as err:
+            kg.msd(h, x, 50, 2, 1.0)
+        assert err.value.status == -5
+    # the handle stays usable
+    assert _rel_per_vector(kg.dos_moments(h, phi, 300), want) < TOL_MOMENTS
+
+
 def test_sigma_pipeline_matches_oracle():
     """sigma^GK (Eq. 6) from VAC moments and sigma^E1 / sigma^E2 (Eqs. 9, 11) from MSD
     moments on the 201-point energy grid: GPU moments + library sums against oracle
