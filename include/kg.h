@@ -357,6 +357,18 @@ kg_status kg_sigma_sc(const double* sigma, int n_times, int n_e, double dt_fs, d
  * [m + 1 + n] = (a_0..a_m, b_1..b_n).  KG_EINVAL when n_points < m + 1 + n. */
 kg_status kg_pade_fit(const double* t, const double* y, int n_points, int m, int n, double* coef_out);
 
+/* The fit of Eq. 58 with every denominator coefficient b_k >= 0, so the approximant has no
+ * pole for t >= 0 (the free linearised fit can put one among flat, noisy late-time data),
+ * and on the true residual sum (R(t_i) - y_i)^2 rather than the linearised one.  Starting
+ * points come from Sanathanan-Koerner reweighting of the bounded linearised problem (rows
+ * divided by the previous pass's denominator until the weights settle; every pass solved
+ * exactly over the 2^n sets of b_k held at 0), begun from four weight profiles
+ * (1 + |t| / s)^-n, s = infinity, t_max, t_max / 10, t_max / 100; each is refined by
+ * projected Levenberg-Marquardt and the smallest residual wins.  n <= 8.  Not in the paper:
+ * a safeguard of the Eq. 58 fit.  Same layout and errors as kg_pade_fit. */
+kg_status kg_pade_fit_positive(const double* t, const double* y, int n_points, int m, int n,
+                               double* coef_out);
+
 /* Value and derivative d/dt of the fitted approximant (for sigma^E1 = e^2 rho d(DX^2)/(2 dt)). */
 kg_status kg_pade_eval(const double* coef, int m, int n, const double* t, int n_points,
                        double* value_out, double* deriv_out);

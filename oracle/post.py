@@ -122,6 +122,44 @@ def pade_fit(t, y, m: int = 2, n: int = 2):
     return x / s
 
 
+def pade_fit_positive(t, y, m: int = 2, n: int = 2, passes: int = 100):
+    """The fit of pade_fit with every b_k >= 0 (no pole for t >= 0) on the true residual
+    sum (R(t_i) - y_i)^2.  Starting points: Sanathanan-Koerner reweighting of the bounded
+    linearised problem (scipy.optimize.lsq_linear; rows divided by the previous pass's
+    denominator until the weights settle) from the weight profiles (1 + |t| / s)^-n,
+    s = inf, t_max, t_max/10, t_max/100; each refined by bounded nonlinear least squares
+    (scipy.optimize.least_squares); the smallest residual is returned."""
+    from scipy.optimize import least_squares, lsq_linear
+    t = np.asarray(t, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    cols = [t ** j for j in range(m + 1)] + [-y * t ** k for k in range(1, n + 1)]
+    a = np.stack(cols, axis=1)
+    lb = np.concatenate([np.full(m + 1, -np.inf), np.zeros(n)])
+    ub = np.full(m + 1 + n, np.inf)
+    t_max = np.max(np.abs(t))
+    best, best_r = None, np.inf
+    for s_start in [np.inf, t_max, t_max / 10, t_max / 100]:
+        w = (1.0 + np.abs(t) / s_start) ** (-n)
+        x = None
+        for _ in range(passes):
+            aw = a * w[:, None]
+            s = np.linalg.norm(aw, axis=0)
+            x = lsq_linear(aw / s, y * w, bounds=(lb * s, ub), method="bvls", tol=1e-15).x / s
+            den = 1.0 + sum(x[m + k] * t ** k for k in range(1, n + 1))
+            w_new = 1.0 / den
+            done = np.max(np.abs(w_new - w) / w) < 1e-12
+            w = w_new
+            if done:
+                break
+        x = np.maximum(x, lb)
+        fit = least_squares(lambda c: pade_value(c, t, m, n) - y, x, bounds=(lb, ub), x_scale="jac",
+                            method="trf", ftol=1e-15, xtol=1e-15, gtol=1e-15, max_nfev=5000)
+        r = np.sum(fit.fun ** 2)
+        if r < best_r:
+            best, best_r = fit.x, r
+    return best
+
+
 def pade_value(coef, t, m: int = 2, n: int = 2):
     t = np.asarray(t, dtype=np.float64)
     num = sum(coef[j] * t ** j for j in range(m + 1))

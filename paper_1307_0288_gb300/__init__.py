@@ -86,6 +86,7 @@ ABI = [
     ("kg_ballistic", _I, [_P, _P, _I, _I, _D, _D, _P, _P]),
     ("kg_sigma_sc", _I, [_P, _I, _I, _D, _D, _D, _P, _P]),
     ("kg_pade_fit", _I, [_P, _P, _I, _I, _I, _P]),
+    ("kg_pade_fit_positive", _I, [_P, _P, _I, _I, _I, _P]),
     ("kg_pade_eval", _I, [_P, _I, _I, _P, _I, _P, _P]),
     ("kg_mlp_create", _I, [_P, _P, ctypes.POINTER(_P)]),
     ("kg_mlp_destroy", None, [_P]),
@@ -543,12 +544,13 @@ def sigma_sc(sigma, dt_fs: float, t1_fs: float, t2_fs: float):
     return mx, av
 
 
-def pade_fit(t, y, m: int = 2, n: int = 2) -> np.ndarray:
-    """kg_pade_fit -> (a_0..a_m, b_1..b_n)  (Eq. 58)."""
+def pade_fit(t, y, m: int = 2, n: int = 2, positive: bool = False) -> np.ndarray:
+    """kg_pade_fit (or kg_pade_fit_positive: every b_k >= 0) -> (a_0..a_m, b_1..b_n)  (Eq. 58)."""
     t = np.ascontiguousarray(t, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
     c = np.zeros(m + 1 + n)
-    _check(lib().kg_pade_fit(t.ctypes.data, y.ctypes.data, len(t), m, n, c.ctypes.data))
+    fn = lib().kg_pade_fit_positive if positive else lib().kg_pade_fit
+    _check(fn(t.ctypes.data, y.ctypes.data, len(t), m, n, c.ctypes.data))
     return c
 
 

@@ -304,52 +304,245 @@ kg_status kg_sigma_sc(const double* sigma, int n_times, int n_e, double dt_fs, d
 //   y(t) = sum_{j<=m} a_j t^j / (1 + sum_{1<=k<=n} b_k t^k),
 // linearised as sum_j a_j t^j - y sum_k b_k t^k = y and solved in the least-squares sense
 // with Householder QR on the columns scaled to unit norm.  coef_out = (a_0..a_m, b_1..b_n).
-kg_status kg_pade_fit(const double* t, const double* y, int n_points, int m, int n, double* coef_out) {
+// Least squares min |A x - rhs| over the columns listed in cols (the others are 0), with
+// Householder QR on those columns scaled to unit norm.  A is row-major [rows][p].
+static kg_status ls_columns(const std::vector<double>& A, const double* rhs, int rows, int p,
+                            const std::vector<int>& cols, double* x_out) {
+    const int q = (int)cols.size();
+    std::vector<double> M((size_t)rows * q), b(rhs, rhs + rows), scale(q, 0.0), x(q, 0.0);
+    for (int i = 0; i < rows; i++)
+        for (int c = 0; c < q; c++) M[(size_t)i * q + c] = A[(size_t)i * p + cols[c]];
+    for (int c = 0; c < q; c++) {
+        double s = 0.0;
+        for (int i = 0; i < rows; i++) s += M[(size_t)i * q + c] * M[(size_t)i * q + c];
+        scale[c] = s > 0 ? std::sqrt(s) : 1.0;
+        for (int i = 0; i < rows; i++) M[(size_t)i * q + c] /= scale[c];
+    }
+    for (int c = 0; c < q; c++) {
+        double norm = 0.0;
+        for (int i = c; i < rows; i++) norm += M[(size_t)i * q + c] * M[(size_t)i * q + c];
+        norm = std::sqrt(norm);
+        if (norm == 0.0) return fail(KG_EINVAL, "kg_pade_fit: rank-deficient system");
+        const double alpha = M[(size_t)c * q + c] > 0 ? -norm : norm;
+        std::vector<double> v(rows - c);
+        for (int i = c; i < rows; i++) v[i - c] = M[(size_t)i * q + c];
+        v[0] -= alpha;
+        double vv = 0.0;
+        for (double w : v) vv += w * w;
+        if (vv == 0.0) continue;
+        for (int cc = c; cc < q; cc++) {
+            double d = 0.0;
+            for (int i = c; i < rows; i++) d += v[i - c] * M[(size_t)i * q + cc];
+            d = 2.0 * d / vv;
+            for (int i = c; i < rows; i++) M[(size_t)i * q + cc] -= d * v[i - c];
+        }
+        double d = 0.0;
+        for (int i = c; i < rows; i++) d += v[i - c] * b[i];
+        d = 2.0 * d / vv;
+        for (int i = c; i < rows; i++) b[i] -= d * v[i - c];
+    }
+    for (int c = q - 1; c >= 0; c--) {
+        double s = b[c];
+        for (int cc = c + 1; cc < q; cc++) s -= M[(size_t)c * q + cc] * x[cc];
+        x[c] = s / M[(size_t)c * q + c];
+    }
+    for (int c = 0; c < p; c++) x_out[c] = 0.0;
+    for (int c = 0; c < q; c++) x_out[cols[c]] = x[c] / scale[c];
+    return KG_OK;
+}
+
+// The linearised system of Eq. 58: row i is (t^0..t^m, -y t^1..-y t^n), right-hand side y.
+static std::vector<double> pade_system(const double* t, const double* y, int n_points, int m, int n) {
     const int p = m + 1 + n;
-    if (!t || !y || !coef_out || m < 0 || n < 0 || n_points < p) return fail(KG_EINVAL, "kg_pade_fit: bad arguments");
-    std::vector<double> A((size_t)n_points * p), b(y, y + n_points), scale(p, 0.0);
+    std::vector<double> A((size_t)n_points * p);
     for (int i = 0; i < n_points; i++) {
         double tp = 1.0;
         for (int j = 0; j <= m; j++, tp *= t[i]) A[(size_t)i * p + j] = tp;
         tp = t[i];
         for (int k = 1; k <= n; k++, tp *= t[i]) A[(size_t)i * p + m + k] = -y[i] * tp;
     }
-    for (int c = 0; c < p; c++) {
-        double s = 0.0;
-        for (int i = 0; i < n_points; i++) s += A[(size_t)i * p + c] * A[(size_t)i * p + c];
-        scale[c] = s > 0 ? std::sqrt(s) : 1.0;
-        for (int i = 0; i < n_points; i++) A[(size_t)i * p + c] /= scale[c];
+    return A;
+}
+
+kg_status kg_pade_fit(const double* t, const double* y, int n_points, int m, int n, double* coef_out) {
+    const int p = m + 1 + n;
+    if (!t || !y || !coef_out || m < 0 || n < 0 || n_points < p) return fail(KG_EINVAL, "kg_pade_fit: bad arguments");
+    const std::vector<double> A = pade_system(t, y, n_points, m, n);
+    std::vector<int> cols(p);
+    for (int c = 0; c < p; c++) cols[c] = c;
+    return ls_columns(A, y, n_points, p, cols, coef_out);
+}
+
+// Bounded least squares min |W (A x - y)| with every b_k >= 0 (W = diag(w)).  The problem is
+// convex; its minimiser solves the unconstrained problem with some set of b_k held at 0, so
+// all 2^n such sets are solved and the feasible solution with the smallest residual kept.
+static kg_status pade_bounded(const std::vector<double>& A, const double* y, const std::vector<double>& w,
+                              int n_points, int m, int n, double* x_out) {
+    const int p = m + 1 + n;
+    std::vector<double> Aw(A.size()), yw(n_points), x(p);
+    for (int i = 0; i < n_points; i++) {
+        yw[i] = w[i] * y[i];
+        for (int c = 0; c < p; c++) Aw[(size_t)i * p + c] = w[i] * A[(size_t)i * p + c];
     }
-    // Householder QR: A = Q R, then R x = Q^T b
-    for (int c = 0; c < p; c++) {
-        double norm = 0.0;
-        for (int i = c; i < n_points; i++) norm += A[(size_t)i * p + c] * A[(size_t)i * p + c];
-        norm = std::sqrt(norm);
-        if (norm == 0.0) return fail(KG_EINVAL, "kg_pade_fit: rank-deficient system");
-        const double alpha = A[(size_t)c * p + c] > 0 ? -norm : norm;
-        std::vector<double> v(n_points - c);
-        for (int i = c; i < n_points; i++) v[i - c] = A[(size_t)i * p + c];
-        v[0] -= alpha;
-        double vv = 0.0;
-        for (double q : v) vv += q * q;
-        if (vv == 0.0) continue;
-        for (int cc = c; cc < p; cc++) {
-            double d = 0.0;
-            for (int i = c; i < n_points; i++) d += v[i - c] * A[(size_t)i * p + cc];
-            d = 2.0 * d / vv;
-            for (int i = c; i < n_points; i++) A[(size_t)i * p + cc] -= d * v[i - c];
+    double best_r = -1.0;
+    for (unsigned mask = 0; mask < (1u << n); mask++) {   // bit k set: b_{k+1} held at 0
+        std::vector<int> cols;
+        for (int j = 0; j <= m; j++) cols.push_back(j);
+        for (int k = 0; k < n; k++)
+            if (!(mask & (1u << k))) cols.push_back(m + 1 + k);
+        if (ls_columns(Aw, yw.data(), n_points, p, cols, x.data()) != KG_OK) continue;
+        bool feasible = true;
+        for (int k = 0; k < n; k++) feasible &= x[m + 1 + k] >= 0.0;
+        if (!feasible) continue;
+        double r = 0.0;
+        for (int i = 0; i < n_points; i++) {
+            double e = -yw[i];
+            for (int c = 0; c < p; c++) e += Aw[(size_t)i * p + c] * x[c];
+            r += e * e;
         }
-        double d = 0.0;
-        for (int i = c; i < n_points; i++) d += v[i - c] * b[i];
-        d = 2.0 * d / vv;
-        for (int i = c; i < n_points; i++) b[i] -= d * v[i - c];
+        if (best_r < 0 || r < best_r) {
+            best_r = r;
+            for (int c = 0; c < p; c++) x_out[c] = x[c];
+        }
     }
-    for (int c = p - 1; c >= 0; c--) {
-        double s = b[c];
-        for (int cc = c + 1; cc < p; cc++) s -= A[(size_t)c * p + cc] * coef_out[cc];
-        coef_out[c] = s / A[(size_t)c * p + c];
+    clear_error();
+    return best_r < 0 ? fail(KG_EINVAL, "kg_pade_fit_positive: no solvable column set") : KG_OK;
+}
+
+// Residuals R(t_i) - y_i of the approximant x = (a_0..a_m, b_1..b_n) and, when J is not null,
+// their Jacobian [n_points][p]: dR/da_j = t^j / D, dR/db_k = -R t^k / D.  Returns sum r^2.
+static double pade_residuals(const double* t, const double* y, int n_points, int m, int n, const double* x,
+                             double* r, double* J) {
+    const int p = m + 1 + n;
+    double sum = 0.0;
+    for (int i = 0; i < n_points; i++) {
+        double num = 0.0, den = 1.0, tp = 1.0;
+        for (int j = 0; j <= m; j++, tp *= t[i]) num += x[j] * tp;
+        tp = t[i];
+        for (int k = 1; k <= n; k++, tp *= t[i]) den += x[m + k] * tp;
+        const double R = num / den, e = R - y[i];
+        if (r) r[i] = e;
+        sum += e * e;
+        if (J) {
+            tp = 1.0;
+            for (int j = 0; j <= m; j++, tp *= t[i]) J[(size_t)i * p + j] = tp / den;
+            tp = t[i];
+            for (int k = 1; k <= n; k++, tp *= t[i]) J[(size_t)i * p + m + k] = -R * tp / den;
+        }
     }
-    for (int c = 0; c < p; c++) coef_out[c] /= scale[c];
+    return sum;
+}
+
+// Projected Levenberg-Marquardt (Levenberg 1944, Marquardt 1963) on sum (R(t_i) - y_i)^2
+// with b_k >= 0, from x (updated in place).  A b_k at 0 whose gradient points below 0 is held
+// fixed for the step; every trial point is projected onto b >= 0.  Returns the final sum.
+static double pade_refine(const double* t, const double* y, int n_points, int m, int n, double* x) {
+    const int p = m + 1 + n;
+    std::vector<double> r(n_points), J((size_t)n_points * p), xt(p);
+    double f = pade_residuals(t, y, n_points, m, n, x, r.data(), J.data());
+    double lambda = 1e-3;
+    for (int it = 0; it < 500 && lambda < 1e16; it++) {
+        std::vector<double> H((size_t)p * p, 0.0), g(p, 0.0);
+        for (int i = 0; i < n_points; i++)
+            for (int c = 0; c < p; c++) {
+                g[c] += J[(size_t)i * p + c] * r[i];
+                for (int d = 0; d < p; d++) H[(size_t)c * p + d] += J[(size_t)i * p + c] * J[(size_t)i * p + d];
+            }
+        std::vector<int> fr;   // free parameters of this step
+        for (int c = 0; c < p; c++)
+            if (!(c > m && x[c] <= 0.0 && g[c] >= 0.0)) fr.push_back(c);
+        const int q = (int)fr.size();
+        // (H + lambda diag H) d = -g on the free set, in Jacobi-scaled variables, by Gaussian elimination
+        std::vector<double> S(q), M((size_t)q * (q + 1));
+        for (int c = 0; c < q; c++) S[c] = H[(size_t)fr[c] * p + fr[c]] > 0 ? 1.0 / std::sqrt(H[(size_t)fr[c] * p + fr[c]]) : 1.0;
+        for (int c = 0; c < q; c++) {
+            for (int d = 0; d < q; d++) M[(size_t)c * (q + 1) + d] = H[(size_t)fr[c] * p + fr[d]] * S[c] * S[d];
+            M[(size_t)c * (q + 1) + c] *= 1.0 + lambda;
+            M[(size_t)c * (q + 1) + q] = -g[fr[c]] * S[c];
+        }
+        bool singular = false;
+        for (int c = 0; c < q && !singular; c++) {
+            int piv = c;
+            for (int d = c + 1; d < q; d++)
+                if (std::fabs(M[(size_t)d * (q + 1) + c]) > std::fabs(M[(size_t)piv * (q + 1) + c])) piv = d;
+            if (M[(size_t)piv * (q + 1) + c] == 0.0) { singular = true; break; }
+            if (piv != c)
+                for (int e = 0; e <= q; e++) std::swap(M[(size_t)c * (q + 1) + e], M[(size_t)piv * (q + 1) + e]);
+            for (int d = c + 1; d < q; d++) {
+                const double fct = M[(size_t)d * (q + 1) + c] / M[(size_t)c * (q + 1) + c];
+                for (int e = c; e <= q; e++) M[(size_t)d * (q + 1) + e] -= fct * M[(size_t)c * (q + 1) + e];
+            }
+        }
+        if (singular) { lambda *= 10.0; continue; }
+        std::vector<double> d(q);
+        for (int c = q - 1; c >= 0; c--) {
+            double v = M[(size_t)c * (q + 1) + q];
+            for (int e = c + 1; e < q; e++) v -= M[(size_t)c * (q + 1) + e] * d[e];
+            d[c] = v / M[(size_t)c * (q + 1) + c];
+        }
+        for (int c = 0; c < p; c++) xt[c] = x[c];
+        for (int c = 0; c < q; c++) xt[fr[c]] += d[c] * S[c];
+        for (int k = 1; k <= n; k++) xt[m + k] = std::max(xt[m + k], 0.0);
+        const double ft = pade_residuals(t, y, n_points, m, n, xt.data(), nullptr, nullptr);
+        if (std::isfinite(ft) && ft < f) {
+            const bool tiny = f - ft <= 1e-15 * f;
+            for (int c = 0; c < p; c++) x[c] = xt[c];
+            f = pade_residuals(t, y, n_points, m, n, x, r.data(), J.data());
+            lambda = std::max(lambda * 0.1, 1e-12);
+            if (tiny) break;
+        } else {
+            lambda *= 10.0;
+        }
+    }
+    return f;
+}
+
+// Eq. 58 with every b_k >= 0 (no pole for t >= 0), fitted to the true residual
+// sum (R(t_i) - y_i)^2.  Starting points: Sanathanan-Koerner reweighting of the linearised
+// problem (the linearised residual of point i is the true one times the denominator D(t_i),
+// so each pass divides row i by D(t_i) of the previous pass, until the weights change by
+// less than 1e-12, at most 100 passes), begun from four weight profiles
+// w_i = (1 + |t_i| / s)^-n, s = infinity, t_max, t_max / 10, t_max / 100.  Each start is
+// refined by projected Levenberg-Marquardt; the one with the smallest residual is returned.
+kg_status kg_pade_fit_positive(const double* t, const double* y, int n_points, int m, int n, double* coef_out) {
+    const int p = m + 1 + n;
+    if (!t || !y || !coef_out || m < 0 || n < 0 || n > 8 || n_points < p)
+        return fail(KG_EINVAL, "kg_pade_fit_positive: bad arguments (n <= 8, n_points >= m + 1 + n)");
+    const std::vector<double> A = pade_system(t, y, n_points, m, n);
+    double t_max = 0.0;
+    for (int i = 0; i < n_points; i++) t_max = std::max(t_max, std::fabs(t[i]));
+    std::vector<double> x(p), best(p);
+    double best_r = -1.0;
+    for (int start = 0; start < 4; start++) {
+        std::vector<double> w(n_points, 1.0);
+        if (start > 0 && t_max > 0) {
+            const double sc = t_max / std::pow(10.0, start - 1);
+            for (int i = 0; i < n_points; i++) w[i] = std::pow(1.0 + std::fabs(t[i]) / sc, -n);
+        }
+        bool solved = false;
+        for (int pass = 0; pass < 100; pass++) {
+            if (pade_bounded(A, y, w, n_points, m, n, x.data()) != KG_OK) break;
+            solved = true;
+            double change = 0.0;
+            for (int i = 0; i < n_points; i++) {
+                double den = 1.0, tp = t[i];
+                for (int k = 1; k <= n; k++, tp *= t[i]) den += x[m + k] * tp;
+                const double wn = 1.0 / den;
+                change = std::max(change, std::fabs(wn - w[i]) / w[i]);
+                w[i] = wn;
+            }
+            if (change < 1e-12) break;
+        }
+        if (!solved) continue;
+        const double r = pade_refine(t, y, n_points, m, n, x.data());
+        if (std::isfinite(r) && (best_r < 0 || r < best_r)) {
+            best_r = r;
+            best = x;
+        }
+    }
+    clear_error();
+    if (best_r < 0) return fail(KG_EINVAL, "kg_pade_fit_positive: no solvable column set");
+    for (int c = 0; c < p; c++) coef_out[c] = best[c];
     return KG_OK;
 }
 

@@ -136,3 +136,12 @@ def test_ballistic_sigma_sc_and_pade_match_oracle():
     assert np.allclose(v1, post.pade_value(c2, tt), rtol=1e-6)
     fd = (post.pade_value(c1, tt + 1e-4) - post.pade_value(c1, tt - 1e-4)) / 2e-4
     assert np.allclose(d1, fd, rtol=1e-5)
+    t2 = np.arange(100) * 20.0 + 200.0
+    y2 = 400.0 * (1.0 - np.exp(-t2 / 600.0)) + rng.normal(scale=4.0, size=100)
+    p1 = kg.pade_fit(t2, y2, positive=True)
+    p2 = post.pade_fit_positive(t2, y2)
+    assert np.all(p1[3:] >= 0)
+    r1 = np.sum((post.pade_value(p1, t2) - y2) ** 2)
+    r2 = np.sum((post.pade_value(p2, t2) - y2) ** 2)
+    assert r1 <= r2 * (1 + 1e-6)
+    assert np.allclose(post.pade_value(p1, t2), post.pade_value(p2, t2), rtol=1e-4)

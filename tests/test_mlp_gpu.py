@@ -70,6 +70,25 @@ def test_adam_training_reduces_loss():
     assert np.all(np.isfinite(net.params()))
 
 
+def test_adam_step_matches_oracle():
+    """Two train steps on the GPU against the oracle's Adam update (Kingma and Ba, 2015)
+    applied to the gradients the GPU reports for the same parameters and batch."""
+    p0 = omlp.init_params(12).astype(np.float32)
+    net = kg.Mlp(p0)
+    x, t = _batch(2048, 5)
+    lr = 1e-3
+    p = p0.astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for step in (1, 2):
+        _, g = net.gradients(x, t)
+        net.train_step(x, t, lr)
+        want, m, v = omlp.adam_step(p, g.astype(np.float64), m, v, step, lr)
+        got = net.params().astype(np.float64)
+        assert np.max(np.abs(got - want)) < 1e-3 * lr, step
+        p = got
+
+
 def test_surrogate_learns_method_sigma_and_is_faster():
     """Reduced surrogate workflow: sigma^GK(E, t) surfaces from the method for 10 vacancy
     concentrations x 3 disorder seeds on 64 x 64-cell sheets; train on 8, predict the 2

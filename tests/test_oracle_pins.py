@@ -469,6 +469,29 @@ def test_mlp_oracle_gradients_match_finite_differences():
         assert abs(fd - g[k]) <= 1e-6 * max(abs(fd), 1e-3), (k, fd, g[k])
 
 
+def test_mlp_oracle_adam_closed_forms():
+    """Adam with bias correction (Kingma and Ba, 2015): under a constant gradient g the
+    corrected moments are exactly g and g^2 at every step, so each step moves a
+    parameter by lr g / (|g| + eps); a gradient that flips sign after one step
+    moves it back by less than lr in the second step."""
+    from oracle import mlp
+    rng = np.random.default_rng(2)
+    flat = rng.normal(size=50)
+    g = rng.normal(size=50)
+    m = np.zeros(50)
+    v = np.zeros(50)
+    lr, eps = 1e-2, 1e-8
+    x = flat.copy()
+    for step in range(1, 6):
+        x_new, m, v = mlp.adam_step(x, g, m, v, step, lr, eps=eps)
+        assert np.allclose(x - x_new, lr * g / (np.abs(g) + eps), rtol=1e-12, atol=1e-15)
+        x = x_new
+    x1, m1, v1 = mlp.adam_step(flat, g, np.zeros(50), np.zeros(50), 1, lr)
+    x2, _, _ = mlp.adam_step(x1, -g, m1, v1, 2, lr)
+    step2 = x2 - x1
+    assert np.all(np.sign(step2) == np.sign(g)) and np.all(np.abs(step2) < lr)
+
+
 def test_mlp_oracle_gelu_and_layout():
     """GELU closed forms (GELU(0) = 0, GELU(z) -> z for large z, GELU' = derivative)
     and the parameter count 3*256 + 256 + 3*(256^2 + 256) + 256 + 1."""
@@ -534,6 +557,35 @@ def test_ballistic_conductance_forms_agree_when_msd_is_quadratic():
     assert np.allclose(length[1:], 2 * v[None, :] * t[1:, None], rtol=1e-12)
     ref = 0.5 * 12.0 * post.H_EV_FS * rho * v
     assert np.allclose(g[1:-1], ref[None, :], rtol=1e-12)
+
+
+def test_pade_fit_positive_kkt():
+    """The bounded fit (b_k >= 0, true residual) returns an exact approximant with positive
+    b unchanged; on noisy saturating data it follows the data to the noise level, and it
+    satisfies the first-order (KKT) conditions of bounded least squares on the true
+    residual: zero gradient J^T r in the free coefficients and a non-negative gradient for
+    every b_k held at 0."""
+    t = np.linspace(1.0, 200.0, 60)
+    coef = np.array([0.5, 3.0, 0.02, 0.01, 2e-4])
+    assert np.allclose(post.pade_value(post.pade_fit_positive(t, post.pade_value(coef, t)), t),
+                       post.pade_value(coef, t), rtol=1e-9)
+    rng = np.random.default_rng(7)
+    tt = np.arange(190) * 20.0 + 200.0
+    y = 400.0 * (1.0 - np.exp(-tt / 300.0)) + rng.normal(scale=5.0, size=190)
+    c = post.pade_fit_positive(tt, y)
+    assert np.all(c[3:] >= 0)
+    r = post.pade_value(c, tt) - y
+    assert np.sqrt(np.mean(r ** 2)) < 1.2 * 5.0
+    den = 1.0 + c[3] * tt + c[4] * tt ** 2
+    val = post.pade_value(c, tt)
+    jac = np.stack([tt ** 0 / den, tt / den, tt ** 2 / den, -val * tt / den, -val * tt ** 2 / den], axis=1)
+    grad = jac.T @ r
+    scale = np.linalg.norm(jac, axis=0) * np.linalg.norm(r)
+    for k in range(5):
+        if k >= 3 and c[k] == 0.0:
+            assert grad[k] >= -1e-6 * scale[k]
+        else:
+            assert abs(grad[k]) <= 1e-5 * scale[k], (k, grad[k], scale[k])
 
 
 def test_sigma_sc_definitions():
