@@ -234,6 +234,122 @@ __global__ void __launch_bounds__(kThreads) kpm_gen_kernel(DevH H, const vec2_t<
 }
 
 // --------------------------------------------------------------------------------
+// complex64 KPM steps with 128-bit accesses: for R >= 2 one thread owns the two adjacent
+// vectors (2 r2, 2 r2 + 1) of a site and moves them as one float4, halving the load and
+// store instructions per byte of the HBM-bound FP32 step.  Per-vector partial sums are
+// kept separately, in the [R][NACC] order the reductions expect.
+// --------------------------------------------------------------------------------
+struct Nbr4 {
+    float4 a, b, c, x;
+};
+
+template <int R2>
+__device__ __forceinline__ Nbr4 gather_pair(Idx3 j, int64_t n, int r2, const float4* __restrict__ v) {
+    Nbr4 g;
+    g.a = __ldg(v + (int64_t)j.i0 * R2 + r2);
+    g.b = __ldg(v + (int64_t)j.i1 * R2 + r2);
+    g.c = __ldg(v + (int64_t)j.i2 * R2 + r2);
+    g.x = __ldg(v + n * R2 + r2);
+    return g;
+}
+
+template <int R, bool ONSITE, bool FIRST>
+__global__ void __launch_bounds__(kThreads) kpm_sym_pair_kernel(DevH H, const float4* __restrict__ cur,
+                                                                const float4* prev, float4* out,
+                                                                double* __restrict__ partial) {
+    constexpr int R2 = R / 2;
+    const int64_t n_items = H.n * R2;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int r2 = threadIdx.x & (R2 - 1);
+    const float c = (float)(FIRST ? H.h : 2.0 * H.h);
+    Acc<float> s0, s1, t0, t1;   // <x|x>, <y|x> of vectors 2 r2 and 2 r2 + 1
+    int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    Idx3 nid;
+    if (w < n_items) nid = load_idx(H.idx, H.istride, w / R2);
+    for (; w < n_items; w += stride) {
+        const int64_t n = w / R2;
+        const Nbr4 g = gather_pair<R2>(nid, n, r2, cur);
+        float e = 0.0f;
+        if constexpr (ONSITE) e = (float)((FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n));
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (!FIRST) z = prev[w];
+        if (w + stride < n_items) nid = load_idx(H.idx, H.istride, (w + stride) / R2);
+        float4 y;
+        y.x = hop<float>(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
+        y.y = hop<float>(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
+        y.z = hop<float>(c, g.a.z, g.b.z, g.c.z, e, g.x.z, z.z, ONSITE);
+        y.w = hop<float>(c, g.a.w, g.b.w, g.c.w, e, g.x.w, z.w, ONSITE);
+        out[w] = y;
+        s0.add_prod(g.x.x, g.x.x);
+        s0.add_prod(g.x.y, g.x.y);
+        s1.add_prod(y.x, g.x.x);
+        s1.add_prod(y.y, g.x.y);
+        t0.add_prod(g.x.z, g.x.z);
+        t0.add_prod(g.x.w, g.x.w);
+        t1.add_prod(y.z, g.x.z);
+        t1.add_prod(y.w, g.x.w);
+    }
+    double acc[4] = {s0.value(), s1.value(), t0.value(), t1.value()};
+    block_reduce<R2, 4>(acc, partial + (int64_t)blockIdx.x * R * 2);
+}
+
+template <int R, bool ONSITE, bool FIRST>
+__global__ void __launch_bounds__(kThreads) kpm_gen_pair_kernel(DevH H, const float4* __restrict__ L,
+                                                                const float4* __restrict__ cur,
+                                                                const float4* prev, float4* out,
+                                                                double* __restrict__ partial) {
+    constexpr int NACC = FIRST ? 4 : 2;
+    constexpr int R2 = R / 2;
+    const int64_t n_items = H.n * R2;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int r2 = threadIdx.x & (R2 - 1);
+    const float c = (float)(FIRST ? H.h : 2.0 * H.h);
+    Acc<float> a[2 * NACC];   // vector 2 r2: a[0..NACC), vector 2 r2 + 1: a[NACC..2 NACC)
+    int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    Idx3 nid;
+    if (w < n_items) nid = load_idx(H.idx, H.istride, w / R2);
+    for (; w < n_items; w += stride) {
+        const int64_t n = w / R2;
+        const Nbr4 g = gather_pair<R2>(nid, n, r2, cur);
+        float e = 0.0f;
+        if constexpr (ONSITE) e = (float)((FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n));
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (!FIRST) z = prev[w];
+        const float4 l = __ldg(L + w);
+        if (w + stride < n_items) nid = load_idx(H.idx, H.istride, (w + stride) / R2);
+        float4 y;
+        y.x = hop<float>(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
+        y.y = hop<float>(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
+        y.z = hop<float>(c, g.a.z, g.b.z, g.c.z, e, g.x.z, z.z, ONSITE);
+        y.w = hop<float>(c, g.a.w, g.b.w, g.c.w, e, g.x.w, z.w, ONSITE);
+        out[w] = y;
+        // <L|y> = (l.x y.x + l.y y.y) + i (l.x y.y - l.y y.x), per vector of the pair
+        a[0].add_prod(l.x, y.x);
+        a[0].add_prod(l.y, y.y);
+        a[1].add_prod(l.x, y.y);
+        a[1].add_prod(-l.y, y.x);
+        a[NACC].add_prod(l.z, y.z);
+        a[NACC].add_prod(l.w, y.w);
+        a[NACC + 1].add_prod(l.z, y.w);
+        a[NACC + 1].add_prod(-l.w, y.z);
+        if constexpr (FIRST) {
+            a[2].add_prod(l.x, g.x.x);
+            a[2].add_prod(l.y, g.x.y);
+            a[3].add_prod(l.x, g.x.y);
+            a[3].add_prod(-l.y, g.x.x);
+            a[NACC + 2].add_prod(l.z, g.x.z);
+            a[NACC + 2].add_prod(l.w, g.x.w);
+            a[NACC + 3].add_prod(l.z, g.x.w);
+            a[NACC + 3].add_prod(-l.w, g.x.z);
+        }
+    }
+    double acc[2 * NACC];
+#pragma unroll
+    for (int q = 0; q < 2 * NACC; q++) acc[q] = a[q].value();
+    block_reduce<R2, 2 * NACC>(acc, partial + (int64_t)blockIdx.x * R * NACC);
+}
+
+// --------------------------------------------------------------------------------
 // Reductions of per-block partials into moments (fixed order => deterministic).
 // --------------------------------------------------------------------------------
 
@@ -537,10 +653,24 @@ static int one_wave_grid(K kernel, int64_t n_items) {
     if (b_) { constexpr bool NAME = true; __VA_ARGS__; } \
     else { constexpr bool NAME = false; __VA_ARGS__; }
 
+// complex64 blocks of R >= 2 vectors use the paired (float4) kernels.
+template <typename T>
+constexpr bool kPaired = sizeof(T) == sizeof(float);
+
 template <typename T>
 cudaError_t launch_kpm_sym(const DevH& H, int R, bool first, const vec2_t<T>* cur, const vec2_t<T>* prev,
                            vec2_t<T>* out, double* partial, int grid, cudaStream_t s) {
     const bool ons = H.onsite != nullptr;
+    if constexpr (kPaired<T>) {
+        if (R >= 2) {
+            const float4* c4 = reinterpret_cast<const float4*>(cur);
+            const float4* p4 = reinterpret_cast<const float4*>(prev);
+            float4* o4 = reinterpret_cast<float4*>(out);
+            KG_DISPATCH_R(R, if constexpr (RR >= 2) { KG_BOOL(ons, ON, KG_BOOL(first, FI,
+                kpm_sym_pair_kernel<RR, ON, FI><<<grid, kThreads, 0, s>>>(H, c4, p4, o4, partial))) });
+            return cudaGetLastError();
+        }
+    }
     KG_DISPATCH_R(R, KG_BOOL(ons, ON, KG_BOOL(first, FI,
         kpm_sym_kernel<T, RR, ON, FI><<<grid, kThreads, 0, s>>>(H, cur, prev, out, partial))));
     return cudaGetLastError();
@@ -551,6 +681,17 @@ cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const vec2_t<T>* L,
                            const vec2_t<T>* prev, vec2_t<T>* out, double* partial, int grid,
                            cudaStream_t s) {
     const bool ons = H.onsite != nullptr;
+    if constexpr (kPaired<T>) {
+        if (R >= 2) {
+            const float4* l4 = reinterpret_cast<const float4*>(L);
+            const float4* c4 = reinterpret_cast<const float4*>(cur);
+            const float4* p4 = reinterpret_cast<const float4*>(prev);
+            float4* o4 = reinterpret_cast<float4*>(out);
+            KG_DISPATCH_R(R, if constexpr (RR >= 2) { KG_BOOL(ons, ON, KG_BOOL(first, FI,
+                kpm_gen_pair_kernel<RR, ON, FI><<<grid, kThreads, 0, s>>>(H, l4, c4, p4, o4, partial))) });
+            return cudaGetLastError();
+        }
+    }
     KG_DISPATCH_R(R, KG_BOOL(ons, ON, KG_BOOL(first, FI,
         kpm_gen_kernel<T, RR, ON, FI><<<grid, kThreads, 0, s>>>(H, L, cur, prev, out, partial))));
     return cudaGetLastError();
@@ -559,6 +700,30 @@ cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const vec2_t<T>* L,
 template <typename T>
 int kpm_grid(const DevH& H, int R, bool sym) {
     const bool ons = H.onsite != nullptr;
+    if constexpr (kPaired<T>) {
+        if (R >= 2) {
+            const int64_t pairs = H.n * (R / 2);
+            int g = stream_grid(pairs);
+            auto pick = [&](auto k) { g = one_wave_grid(k, pairs); };
+            switch (R) {
+#define KG_PAIR_GRID_CASE(RV)                                                                  \
+                case RV:                                                                      \
+                    if (sym) {                                                                \
+                        if (ons) pick(kpm_sym_pair_kernel<RV, true, false>);                  \
+                        else pick(kpm_sym_pair_kernel<RV, false, false>);                     \
+                    } else {                                                                  \
+                        if (ons) pick(kpm_gen_pair_kernel<RV, true, false>);                  \
+                        else pick(kpm_gen_pair_kernel<RV, false, false>);                     \
+                    }                                                                         \
+                    break;
+                KG_PAIR_GRID_CASE(2) KG_PAIR_GRID_CASE(4) KG_PAIR_GRID_CASE(8)
+                KG_PAIR_GRID_CASE(16) KG_PAIR_GRID_CASE(32) KG_PAIR_GRID_CASE(64)
+#undef KG_PAIR_GRID_CASE
+                default: break;
+            }
+            return g;
+        }
+    }
     const int64_t items = H.n * R;
     int g = stream_grid(items);
     auto pick = [&](auto k) { g = one_wave_grid(k, items); };
