@@ -517,6 +517,7 @@ def run_surrogate(args):
     y = torch.zeros(n, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         net.forward(x, out=y)
+    launches0 = net.launches()
     net.timing_enable(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -532,6 +533,7 @@ def run_surrogate(args):
     ms = e0.elapsed_time(e1)
     tm = net.timing_read()
     net.timing_enable(False)
+    launches = net.launches() - launches0
     flop_sample = 2 * (3 * 256 + 3 * 256 * 256 + 256)
     # end to end: host inputs and outputs
     xh = x.cpu().pin_memory()
@@ -552,7 +554,14 @@ def run_surrogate(args):
     train_s = (time.perf_counter() - t0) / 10
     peaks = _peaks()
     peak = peaks.get("bf16_tflops", 1900.0)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved = tm["gemm_flop"] / (tm["gemm_ms"] * 1e-3) / 1e12
+    # The 256 x 256 layers move 2 x 512 B of BF16 activations per row for 2 x 131,072 flop:
+    # 128 flop/B, below the GB300's ~290 flop/B balance, so HBM bounds them.  Algorithmic
+    # bytes per forward: layers 2-3 read and write the activations, layer 4 reads them and
+    # writes y (its output layer is fused), plus the three BF16 weight matrices.
+    gemm_bytes = (2 * (2 * n * 256 * 2) + n * 256 * 2 + n * 4 + 3 * 256 * 256 * 2) * args.steps
+    achieved_gbs = gemm_bytes / (tm["gemm_ms"] * 1e-3) / 1e9
     line = {
         "metric": "surrogate sigma(E,t) predictions/s", "value": n * args.steps / (ms * 1e-3),
         "unit": "samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -560,15 +569,19 @@ def run_surrogate(args):
         "dtype": "bf16", "data": "synthetic",
         "config": {"workload": SURROGATE_WORKLOAD, "batch": n, "hidden": [256] * 4,
                    "l2": "activations 1M x 256 x 2 B = 512 MB per layer, larger than L2"},
-        "roofline": {"bound": "tensor", "kernel": "umma_gemm_kernel (tcgen05 BF16 128x256 tiles)",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"
-                     if "bf16_tflops" in peaks else "fallback",
+        "roofline": {"bound": "hbm",
+                     "kernel": "umma_persistent_kernel (tcgen05 BF16, 1M x 256 x 256 per layer, 3 layers)",
+                     "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
+                     "traffic": None, "peak_source": "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback",
+                     "algorithmic_bytes_per_step": gemm_bytes / args.steps,
+                     "tensor": {"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"
+                                if "bf16_tflops" in peaks else "fallback"},
                      "gemm_ms_per_step": tm["gemm_ms"] / args.steps,
                      "gemm_share_of_step": tm["gemm_ms"] / ms},
         "model_tflops": flop_sample * n * args.steps / (ms * 1e-3) / 1e12,
         "train_step_ms_65536": train_s * 1e3,
-        "gpu_launches": int(tm["gemm_launches"] / 3 * 5),
+        "gpu_launches": launches,
         "clocks": clk,
         "e2e": {"value": n / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": n * 12,
                 "d2h_bytes_per_step": n * 4, "seconds": e2e_s},

@@ -3,8 +3,9 @@
 Network: 3 inputs -> 4 hidden layers of 256 GELU units -> 1 output,
     z_1 = W_1 x + b_1,   a_l = GELU(z_l),   z_{l+1} = W_{l+1} a_l + b_{l+1},
     y = w_5 . a_4 + b_5,
-loss = mean over the batch of (y - t)^2.  GELU(z) = z Phi(z) with the standard
-normal CDF Phi(z) = (1 + erf(z / sqrt 2)) / 2, GELU'(z) = Phi(z) + z phi(z).
+loss = mean over the batch of (y - t)^2.  GELU in its tanh form (Hendrycks and
+Gimpel, 2016): GELU(z) = z (1 + tanh(u)) / 2, u = sqrt(2/pi) (z + 0.044715 z^3),
+the published approximation of z Phi(z) (Phi the standard normal CDF).
 
 The surrogate is not part of the paper; it predicts sigma(E, t) curves that the
 method generates.  Parameters use one flat FP32/FP64 layout shared with the
@@ -15,7 +16,6 @@ Parity: pinned by central finite differences of the loss (tests).
 from __future__ import annotations
 
 import numpy as np
-from scipy.special import erf
 
 HIDDEN = 256
 N_IN = 3
@@ -62,12 +62,18 @@ def init_params(seed: int, hidden: int = HIDDEN) -> np.ndarray:
     return pack(p, hidden).astype(np.float32).astype(np.float64)
 
 
+GELU_K = np.sqrt(2.0 / np.pi)
+GELU_C = 0.044715
+
+
 def gelu(z):
-    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+    return 0.5 * z * (1.0 + np.tanh(GELU_K * (z + GELU_C * z ** 3)))
 
 
 def gelu_grad(z):
-    return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+    """d GELU / dz of the tanh form."""
+    t = np.tanh(GELU_K * (z + GELU_C * z ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * GELU_K * (1.0 + 3.0 * GELU_C * z * z)
 
 
 def forward(flat, x, hidden: int = HIDDEN, keep: bool = False):

@@ -493,11 +493,16 @@ def test_mlp_oracle_adam_closed_forms():
 
 
 def test_mlp_oracle_gelu_and_layout():
-    """GELU closed forms (GELU(0) = 0, GELU(z) -> z for large z, GELU' = derivative)
+    """GELU closed forms (GELU(0) = 0, GELU(z) -> z for large z, GELU' = derivative, the tanh
+    form within 5e-4 of z Phi(z))
     and the parameter count 3*256 + 256 + 3*(256^2 + 256) + 256 + 1."""
     from oracle import mlp
+    from scipy.special import erf
     assert mlp.gelu(np.array([0.0]))[0] == 0.0
     assert abs(mlp.gelu(np.array([10.0]))[0] - 10.0) < 1e-12
+    zz = np.linspace(-6, 6, 2001)
+    exact = 0.5 * zz * (1.0 + erf(zz / np.sqrt(2.0)))        # z Phi(z), which the tanh form approximates
+    assert np.max(np.abs(mlp.gelu(zz) - exact)) < 5e-4
     z = np.linspace(-4, 4, 41)
     fd = (mlp.gelu(z + 1e-6) - mlp.gelu(z - 1e-6)) / 2e-6
     assert np.max(np.abs(fd - mlp.gelu_grad(z))) < 1e-8
