@@ -3,8 +3,11 @@
 // and Adam.  The surrogate is not part of the paper; it is trained on sigma(E, t) curves
 // the method generates.
 //
-// The three 256 x 256 layers are dense contractions and run on the 5th-generation tensor
-// cores: one hand-written tcgen05 GEMM kernel D[128 x 256] = A[128 x K] B[256 x K]^T with
+// Batch inference runs the whole network in one persistent kernel (mlp_fused_kernel,
+// below): activations stay in shared memory and TMEM, weights stream from L2.
+//
+// Training: the three 256 x 256 layers are dense contractions and run on the 5th-generation
+// tensor cores: one hand-written tcgen05 GEMM kernel D[128 x 256] = A[128 x K] B[256 x K]^T with
 // BF16 operands staged (by all threads, 16-byte vector loads) in shared memory in the
 // 128-byte-swizzled K-major layout, the FP32 accumulator in tensor memory (TMEM, 256
 // columns), a two-stage pipeline whose stages are released by tcgen05.commit arrivals
@@ -86,8 +89,9 @@ constexpr float kGeluK = 0.7978845608028654f;   // sqrt(2 / pi)
 constexpr float kGeluC = 0.044715f;
 
 __device__ __forceinline__ float gelu(float z) {
-    const float u = kGeluK * fmaf(kGeluC * z, z * z, z);
-    return 0.5f * z * (1.0f + tanh_hw(u));
+    const float u = z * fmaf(kGeluK * kGeluC, z * z, kGeluK);   // sqrt(2/pi) (z + 0.044715 z^3)
+    const float hz = 0.5f * z;
+    return fmaf(hz, tanh_hw(u), hz);
 }
 
 __device__ __forceinline__ float gelu_grad(float z) {
@@ -148,6 +152,17 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
           "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), \
           "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])                                         \
         : "r"(taddr))
+
+#define KG_TMEM_ST32(taddr, v)                                                                       \
+    asm volatile(                                                                                    \
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14," \
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"                 \
+        ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),    \
+          "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), \
+          "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]),        \
+          "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]),        \
+          "r"(v[29]), "r"(v[30]), "r"(v[31])                                                         \
+        : "memory")
 
 template <int EPI>
 __global__ void __launch_bounds__(kGemmThreads, 1) umma_gemm_kernel(GemmArgs g) {
@@ -273,39 +288,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1) umma_gemm_kernel(GemmArgs g) 
     }
 }
 
-// ------------------------------------------------------------------- persistent inference GEMM
+// ------------------------------------------------------------------- inference layout
 //
-// Activations for inference use a core-matrix-tiled layout: the 128-row tile t of an
-// [rows][256] matrix is stored contiguously (64 KB) as [32 k-chunks][128 rows][8 values],
-// i.e. element (row, k) at t*32768 + ((k/8)*128 + row%128)*8 + k%8.  A 64-wide K block of
-// a tile is then one contiguous 16 KB run that a single cp.async.bulk copies into the
-// canonical K-major no-swizzle shared-memory layout (core matrix = 8 rows x 16 B; LBO =
-// distance between core matrices along K, SBO = between 8-row groups), and every
-// epilogue store of 8 values per row is one 16-byte word, coalesced across a warp.
-// The weights use the same layout with 256 rows: [32 k-chunks][256 rows][8].
+// The weights of layers 2-4 are kept for inference in a core-matrix-tiled layout,
+// [32 k-chunks][256 rows][8 values] per layer: a 64-wide K block is one contiguous 32 KB
+// run that a single cp.async.bulk copies into the canonical K-major no-swizzle
+// shared-memory layout (core matrix = 8 rows x 16 B; LBO = distance between core matrices
+// along K, SBO = between 8-row groups).  Activation tiles in shared memory use the same
+// layout with 128 rows, [32 k-chunks][128 rows][8], so that every store of 8 values of a
+// row is one 16-byte word and a warp's 32 rows are conflict-free.
 
-__host__ __device__ constexpr int64_t tiled_index(int64_t row, int col) {
-    return (row >> 7) * (128 * H) + ((int64_t)(col >> 3) * 128 + (row & 127)) * 8 + (col & 7);
-}
-
-constexpr int kPThreads = 320;          // warps 0-7 epilogue, 8 loads, 9 MMA + TMEM
-constexpr int kPWBytes = H * H * 2;     // 128 KB
-constexpr int kPAtomBytes = BM * BK * 2;   // 16 KB
-constexpr int kPSlots = 4;
-constexpr int kPSmem = kPWBytes + kPSlots * kPAtomBytes + 2 * 2 * BM * 4 + 256 + 1024;
-
-struct PArgs {
-    const __nv_bfloat16* a_tiled;   // [n_tiles][32][128][8]
-    int64_t n_tiles;
-    const __nv_bfloat16* w_tiled;   // [32][256][8]
-    const float* bias;              // [256]
-    __nv_bfloat16* out_tiled;       // next layer's activations (null when the output is fused)
-    const float* w5;                // fused output layer: y = w5 . GELU(z) + b5
-    const float* b5;                // device pointer to b5
-    float* y;
-    int64_t n_valid;
-    int* error;
-};
+constexpr int kPThreads = 320;          // warps 0-7 compute, 8 loads, 9 MMA + TMEM
 
 // No-swizzle K-major descriptor (layout type 0) with the given LBO / SBO in bytes.
 __device__ __forceinline__ uint64_t ns_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -346,31 +339,62 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <bool FUSE_OUT>
-__global__ void __launch_bounds__(kPThreads, 1) umma_persistent_kernel(PArgs p) {
+// ------------------------------------------------------------------- fused inference
+//
+// The whole network for batch inference in one persistent kernel, so activations never
+// leave the SM.  A CTA takes 128-row tiles in pairs (X, Y).  Shared memory holds the two
+// tiles' BF16 activations (2 x 64 KB, the canonical K-major no-swizzle layout of the
+// tiled format) and a ring of three 32 KB weight blocks (64 K values of one 256 x 256
+// layer); TMEM holds one 128 x 256 FP32 accumulator per tile (all 512 columns).
+//   warps 0-7  layer 1 (3 -> 256, CUDA cores) straight into the tile buffer, then every
+//              epilogue: GELU from TMEM back into the tile buffer as the next layer's
+//              operand, and the next layer's bias stored into the accumulator (tcgen05.st)
+//              for its MMAs to accumulate onto; after layer 4 the fused 256 -> 1 output;
+//   warp 8     streams the weight blocks with cp.async.bulk (from L2 after the first tiles),
+//              in the order the MMAs use them: per layer X's four blocks, then Y's;
+//   warp 9     issues the tcgen05 MMAs and owns the TMEM.
+// Per pair the order is L1(X) L1(Y) | M2(X) M2(Y) M3(X) M3(Y) M4(X) M4(Y), and the epilogue
+// of one tile overlaps the other tile's MMAs.  Every wait is bounded.
+constexpr int kFSlots = 3;
+constexpr int kFWAtom = BN * BK * 2;                     // 32 KB: 8 k-chunks x 256 rows x 16 B
+constexpr int kFTile = BM * H * 2;                       // 64 KB
+constexpr int kFSmem = 2 * kFTile + kFSlots * kFWAtom + 2 * 2 * BM * 4 + 128 + 16 + 128;
+
+struct FArgs {
+    const float* x;                  // [rows][3], rows >= n_valid read as zero
+    int64_t n_valid;
+    int64_t n_tiles;                 // 128-row tiles (pairs run past an odd count on zeros)
+    const float* params;             // flat FP32 parameters (W1, b1, ..., w5, b5)
+    const __nv_bfloat16* w_tiled;    // [3][32][256][8] BF16 weights of layers 2..4
+    float* y;                        // [n_valid]
+    int* error;
+};
+
+__global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
-    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t base = (raw + 127u) & ~127u;
     uint8_t* base_ptr = smem_raw + (base - raw);
-    const uint32_t sW = base, sA = base + kPWBytes;
-    float* ypart = (float*)(base_ptr + kPWBytes + kPSlots * kPAtomBytes);   // [2 acc][2 halves][128]
-    const uint32_t bars = base + kPWBytes + kPSlots * kPAtomBytes + 2 * 2 * BM * 4;
-    const uint32_t w_full = bars, a_full = bars + 8, a_empty = bars + 8 * 5, acc_full = bars + 8 * 9,
-                   acc_empty = bars + 8 * 11;
-    uint32_t* tmem_slot = (uint32_t*)(base_ptr + kPWBytes + kPSlots * kPAtomBytes + 2 * 2 * BM * 4 + 8 * 13);
+    const uint32_t sA = base;                                   // tile t at sA + t * kFTile
+    const uint32_t sW = base + 2 * kFTile;                      // slot k at sW + k * kFWAtom
+    float* ypart = (float*)(base_ptr + 2 * kFTile + kFSlots * kFWAtom);   // [2 tiles][2 halves][128]
+    const uint32_t bars = base + 2 * kFTile + kFSlots * kFWAtom + 2 * 2 * BM * 4;
+    const uint32_t w_full = bars, w_empty = bars + 8 * kFSlots, a_ready = bars + 16 * kFSlots,
+                   acc_full = bars + 16 * kFSlots + 16;
+    uint32_t* tmem_slot = (uint32_t*)(base_ptr + 2 * kFTile + kFSlots * kFWAtom + 2 * 2 * BM * 4 + 128);
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t n_pairs = (p.n_tiles + 1) / 2;
 
     if (tid == 0) {
         s_abort = 0;
-        mbar_init(w_full, 1);
-        for (int a = 0; a < kPSlots; a++) {
-            mbar_init(a_full + 8 * a, 1);
-            mbar_init(a_empty + 8 * a, 1);
+        for (int k = 0; k < kFSlots; k++) {
+            mbar_init(w_full + 8 * k, 1);
+            mbar_init(w_empty + 8 * k, 1);
         }
-        for (int b = 0; b < 2; b++) {
-            mbar_init(acc_full + 8 * b, 1);
-            mbar_init(acc_empty + 8 * b, 8);
+        for (int t = 0; t < 2; t++) {
+            mbar_init(a_ready + 8 * t, 8);
+            mbar_init(acc_full + 8 * t, 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -390,169 +414,230 @@ __global__ void __launch_bounds__(kPThreads, 1) umma_persistent_kernel(PArgs p) 
     };
 
     if (warp == 8 && lane == 0) {
-        // loads: the weights once, then the four K blocks of every tile of this CTA
-        expect_tx(w_full, kPWBytes);
-        for (int c = 0; c < kPWBytes / kPAtomBytes; c++)
-            bulk_g2s(sW + c * kPAtomBytes, (const uint8_t*)p.w_tiled + (size_t)c * kPAtomBytes, kPAtomBytes, w_full);
-        int j = 0, last_slot = -1, last_use = 0;
-        for (int64_t t = blockIdx.x; t < p.n_tiles && !s_abort; t += gridDim.x, j++) {
-            for (int a = 0; a < kPSlots; a++) {
-                if (j > 0 && !pwait(a_empty + 8 * a, (j - 1) & 1, &s_abort)) {
-                    give_up();
-                    break;
-                }
-                expect_tx(a_full + 8 * a, kPAtomBytes);
-                bulk_g2s(sA + a * kPAtomBytes, (const uint8_t*)p.a_tiled + ((size_t)t * 4 + a) * kPAtomBytes,
-                         kPAtomBytes, a_full + 8 * a);
-                last_slot = a;
-                last_use = j;
-            }
+        // weight blocks in MMA order: per pair, per layer, per tile, four K blocks
+        int64_t g = 0;
+        for (int64_t pr = blockIdx.x; pr < n_pairs && !s_abort; pr += gridDim.x) {
+            for (int l = 0; l < 3 && !s_abort; l++)
+                for (int t = 0; t < 2 && !s_abort; t++)
+                    for (int k = 0; k < 4; k++, g++) {
+                        const int slot = (int)(g % kFSlots);
+                        const int64_t use = g / kFSlots;
+                        if (use > 0 && !pwait(w_empty + 8 * slot, (uint32_t)((use - 1) & 1), &s_abort)) {
+                            give_up();
+                            break;
+                        }
+                        expect_tx(w_full + 8 * slot, kFWAtom);
+                        bulk_g2s(sW + slot * kFWAtom, (const uint8_t*)p.w_tiled + ((size_t)l * 4 + k) * kFWAtom,
+                                 kFWAtom, w_full + 8 * slot);
+                    }
         }
         // no copy may still be landing when the CTA exits (bounded, ignores the abort flag)
         volatile int never = 0;
-        if (!pwait(w_full, 0, &never)) atomicExch(p.error, 1);
-        if (last_slot >= 0 && !pwait(a_full + 8 * last_slot, last_use & 1, &never)) atomicExch(p.error, 1);
+        for (int64_t q = (g > kFSlots ? g - kFSlots : 0); q < g; q++)
+            if (!pwait(w_full + 8 * (int)(q % kFSlots), (uint32_t)((q / kFSlots) & 1), &never)) atomicExch(p.error, 1);
     } else if (warp == 9 && lane == 0) {
-        // MMA issue: D[acc] = A_tile (128 x 256) * W^T, four K blocks of four K=16 steps
-        if (!pwait(w_full, 0, &s_abort)) give_up();
-        int j = 0;
-        uint32_t last_bar = 0, last_parity = 0;   // barrier of the last commit issued
-        for (int64_t t = blockIdx.x; t < p.n_tiles && !s_abort; t += gridDim.x, j++) {
-            const int acc = j & 1;
-            if (j >= 2 && !pwait(acc_empty + 8 * acc, ((j >> 1) - 1) & 1, &s_abort)) {
-                give_up();
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            bool ok = true;
-            for (int a = 0; a < kPSlots && ok; a++) {
-                if (!pwait(a_full + 8 * a, j & 1, &s_abort)) {
-                    give_up();
-                    ok = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        int64_t g = 0, job[2] = {0, 0};
+        uint32_t last_bar = 0, last_parity = 0;
+        for (int64_t pr = blockIdx.x; pr < n_pairs && !s_abort; pr += gridDim.x) {
+            for (int l = 0; l < 3 && !s_abort; l++)
+                for (int t = 0; t < 2 && !s_abort; t++) {
+                    const int64_t jt = job[t]++;   // job index of tile t: a_ready / acc_full phase
+                    // the tile's operand for this layer is written and its accumulator drained
+                    if (!pwait(a_ready + 8 * t, (uint32_t)(jt & 1), &s_abort)) {
+                        give_up();
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    bool ok = true;
+                    for (int k = 0; k < 4; k++, g++) {
+                        const int slot = (int)(g % kFSlots);
+                        if (!pwait(w_full + 8 * slot, (uint32_t)((g / kFSlots) & 1), &s_abort)) {
+                            give_up();
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-                for (int s = 0; s < BK / 16; s++) {
-                    // A: K block a, k-chunks 2s, 2s+1 (LBO = 128 rows x 16 B, SBO = 8 rows x 16 B)
-                    const uint64_t ad = ns_desc(sA + a * kPAtomBytes + s * 2 * BM * 16, BM * 16, 128);
-                    // B: global k-chunks 8a + 2s, +1 of the 256-row weight tile
-                    const uint64_t bd = ns_desc(sW + (a * 8 + 2 * s) * BN * 16, BN * 16, 128);
-                    const uint32_t accum = (a > 0 || s > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + acc * BN),
-                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(accum)
-                        : "memory");
+                        for (int st = 0; st < BK / 16; st++) {
+                            // A: k-chunks 8k + 2st, +1 of the tile (LBO = 128 rows x 16 B, SBO = 8 rows x 16 B)
+                            const uint64_t ad = ns_desc(sA + t * kFTile + (k * 8 + 2 * st) * BM * 16, BM * 16, 128);
+                            // B: k-chunks 2st, +1 of the 256-row weight block in the slot
+                            const uint64_t bd = ns_desc(sW + slot * kFWAtom + 2 * st * BN * 16, BN * 16, 128);
+                            const uint32_t accum = 1u;   // on top of the bias the epilogue preloaded
+                            asm volatile(
+                                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * BN),
+                                "l"(ad), "l"(bd), "r"(kIdesc), "r"(accum)
+                                : "memory");
+                        }
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                         w_empty + 8 * slot)
+                                     : "memory");
+                        last_bar = w_empty + 8 * slot;
+                        last_parity = (uint32_t)((g / kFSlots) & 1);
+                    }
+                    if (!ok) break;
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     acc_full + 8 * t)
+                                 : "memory");
+                    last_bar = acc_full + 8 * t;
+                    last_parity = (uint32_t)(jt & 1);
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 a_empty + 8 * a)
-                             : "memory");
-                last_bar = a_empty + 8 * a;
-                last_parity = j & 1;
-            }
-            if (!ok) break;
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             acc_full + 8 * acc)
-                         : "memory");
-            last_bar = acc_full + 8 * acc;
-            last_parity = (j >> 1) & 1;
         }
         // every MMA issued must be complete before the TMEM is freed (bounded)
         volatile int never = 0;
         if (last_bar && !pwait(last_bar, last_parity, &never)) atomicExch(p.error, 1);
     } else if (warp < 8) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows) and columns of half w / 4
+        // warp w: TMEM lanes (tile rows) 32 (w % 4) .. + 31, accumulator columns of half w / 4
         const int quarter = warp & 3, half = warp >> 2;
         const int rl = quarter * 32 + lane;
-        int j = 0;
-        for (int64_t t = blockIdx.x; t < p.n_tiles; t += gridDim.x, j++) {
-            const int acc = j & 1;
-            const bool ok = pwait(acc_full + 8 * acc, (j >> 1) & 1, &s_abort);
-            if (!ok) give_up();
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int64_t row = t * BM + rl;
-            float ysum = 0.0f;
-            if (ok) {
+        const float* W1 = p.params + kOffW1;
+        const float* b1 = p.params + kOffB1;
+        const float* w5 = p.params + kOffW5;
+        const float b5 = __ldg(p.params + kOffB5);
+        int64_t job[2] = {0, 0};
+        // The accumulator of a tile starts each layer holding that layer's bias in every
+        // row, so the MMAs accumulate on top of it and the epilogue adds no bias.
+        auto preload_bias = [&](int t, int layer) {
+            const float4* bias4 = (const float4*)(p.params + layer_b(layer));
 #pragma unroll 1
-                for (int cb = 0; cb < 4; cb++) {
-                    const int col0 = half * 128 + cb * 32;
-                    uint32_t v[32];
-                    KG_TMEM_LD32(tmem + acc * BN + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0, v);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int cb = 0; cb < 4; cb++) {
+                const int col0 = half * 128 + cb * 32;
+                uint32_t v[32];
 #pragma unroll
-                    for (int c8 = 0; c8 < 4; c8++) {
+                for (int q = 0; q < 8; q++) {
+                    const float4 b = __ldg(bias4 + col0 / 4 + q);
+                    v[4 * q] = __float_as_uint(b.x);
+                    v[4 * q + 1] = __float_as_uint(b.y);
+                    v[4 * q + 2] = __float_as_uint(b.z);
+                    v[4 * q + 3] = __float_as_uint(b.w);
+                }
+                KG_TMEM_ST32(tmem + t * BN + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0, v);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        };
+        // all eight warps have written the tile's operand and the accumulator's bias: publish
+        auto publish = [&](int t) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(a_ready + 8 * t);
+        };
+        for (int64_t pr = blockIdx.x; pr < n_pairs; pr += gridDim.x) {
+            // layer 1: warp w covers k-chunks 4w .. 4w + 3 (32 columns), lane covers rows
+            // lane + 32 i; the column weights are warp-uniform 16-byte loads
+            for (int t = 0; t < 2; t++) {
+                const int64_t row0 = (2 * pr + t) * BM;
+                float xr[4][3];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int64_t grow = row0 + lane + 32 * i;
+                    xr[i][0] = xr[i][1] = xr[i][2] = 0.f;
+                    if (grow < p.n_valid) {
+                        xr[i][0] = __ldg(p.x + grow * 3 + 0);
+                        xr[i][1] = __ldg(p.x + grow * 3 + 1);
+                        xr[i][2] = __ldg(p.x + grow * 3 + 2);
+                    }
+                }
+#pragma unroll 1
+                for (int cq = 0; cq < 4; cq++) {
+                    const int ch = warp * 4 + cq;                  // k-chunk: columns 8 ch .. 8 ch + 7
+                    float w[24], bb[8];
+                    const float4* w4 = (const float4*)(W1 + ch * 24);
+#pragma unroll
+                    for (int q = 0; q < 6; q++) {
+                        const float4 f = __ldg(w4 + q);
+                        w[4 * q] = f.x;
+                        w[4 * q + 1] = f.y;
+                        w[4 * q + 2] = f.z;
+                        w[4 * q + 3] = f.w;
+                    }
+                    const float4 bl = __ldg((const float4*)(b1 + ch * 8)), bh = __ldg((const float4*)(b1 + ch * 8 + 4));
+                    bb[0] = bl.x; bb[1] = bl.y; bb[2] = bl.z; bb[3] = bl.w;
+                    bb[4] = bh.x; bb[5] = bh.y; bb[6] = bh.z; bb[7] = bh.w;
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
                         uint32_t packed[4];
 #pragma unroll
                         for (int e = 0; e < 8; e += 2) {
-                            const int col = col0 + c8 * 8 + e;
-                            const float g0 = gelu(__uint_as_float(v[c8 * 8 + e]) + p.bias[col]);
-                            const float g1 = gelu(__uint_as_float(v[c8 * 8 + e + 1]) + p.bias[col + 1]);
-                            if constexpr (FUSE_OUT) {
-                                ysum = fmaf(__bfloat162float(__float2bfloat16_rn(g0)), p.w5[col], ysum);
-                                ysum = fmaf(__bfloat162float(__float2bfloat16_rn(g1)), p.w5[col + 1], ysum);
-                            } else {
-                                const __nv_bfloat162 b2 = __floats2bfloat162_rn(g0, g1);
-                                packed[e >> 1] = *(const uint32_t*)&b2;
-                            }
+                            const float v0 = fmaf(w[3 * e], xr[i][0], fmaf(w[3 * e + 1], xr[i][1], fmaf(w[3 * e + 2], xr[i][2], bb[e])));
+                            const float v1 = fmaf(w[3 * e + 3], xr[i][0], fmaf(w[3 * e + 4], xr[i][1],
+                                                  fmaf(w[3 * e + 5], xr[i][2], bb[e + 1])));
+                            const __nv_bfloat162 b2 = __floats2bfloat162_rn(gelu(v0), gelu(v1));
+                            packed[e >> 1] = *(const uint32_t*)&b2;
                         }
-                        if constexpr (!FUSE_OUT) {
-                            const int chunk = (col0 >> 3) + c8;
-                            uint4* dst = (uint4*)(p.out_tiled + t * (int64_t)(BM * H) + ((int64_t)chunk * BM + rl) * 8);
-                            *dst = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                        }
+                        st_shared_v4(sA + t * kFTile + (uint32_t)((ch * BM + lane + 32 * i) * 16),
+                                     make_uint4(packed[0], packed[1], packed[2], packed[3]));
                     }
                 }
+                preload_bias(t, 2);
+                publish(t);
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty + 8 * acc);
-            if constexpr (FUSE_OUT) {
-                ypart[(acc * 2 + half) * BM + rl] = ysum;
-                asm volatile("bar.sync 1, 256;" ::: "memory");
-                if (half == 0 && row < p.n_valid && ok)
-                    p.y[row] = ypart[(acc * 2) * BM + rl] + ypart[(acc * 2 + 1) * BM + rl] + __ldg(p.b5);
-            }
+            // layers 2-4: epilogues.  After an abort every wait returns at once, but all eight
+            // warps still run every iteration, so each reaches every named barrier below.
+            for (int l = 0; l < 3; l++)
+                for (int t = 0; t < 2; t++) {
+                    const bool ok = pwait(acc_full + 8 * t, (uint32_t)(job[t] & 1), &s_abort);
+                    job[t]++;
+                    if (!ok) {
+                        give_up();
+                        if (l == 2) asm volatile("bar.sync 1, 256;" ::: "memory");
+                        continue;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    float ysum = 0.0f;
+#pragma unroll 1
+                    for (int cb = 0; cb < 4; cb++) {
+                        const int col0 = half * 128 + cb * 32;
+                        uint32_t v[32];
+                        KG_TMEM_LD32(tmem + t * BN + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0, v);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (l == 2) {
+                            // output layer on the FP32 activations: y = w5 . GELU(z4) + b5
+                            const float4* w54 = (const float4*)(w5 + col0);
+#pragma unroll
+                            for (int q = 0; q < 8; q++) {
+                                const float4 f = __ldg(w54 + q);
+                                ysum = fmaf(gelu(__uint_as_float(v[4 * q])), f.x, ysum);
+                                ysum = fmaf(gelu(__uint_as_float(v[4 * q + 1])), f.y, ysum);
+                                ysum = fmaf(gelu(__uint_as_float(v[4 * q + 2])), f.z, ysum);
+                                ysum = fmaf(gelu(__uint_as_float(v[4 * q + 3])), f.w, ysum);
+                            }
+                        } else {
+#pragma unroll
+                            for (int c8 = 0; c8 < 4; c8++) {
+                                uint32_t packed[4];
+#pragma unroll
+                                for (int e = 0; e < 8; e += 2) {
+                                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(
+                                        gelu(__uint_as_float(v[c8 * 8 + e])), gelu(__uint_as_float(v[c8 * 8 + e + 1])));
+                                    packed[e >> 1] = *(const uint32_t*)&b2;
+                                }
+                                const int chunk = (col0 >> 3) + c8;
+                                st_shared_v4(sA + t * kFTile + (uint32_t)((chunk * BM + rl) * 16),
+                                             make_uint4(packed[0], packed[1], packed[2], packed[3]));
+                            }
+                        }
+                    }
+                    if (l < 2) {
+                        preload_bias(t, l + 3);
+                        publish(t);
+                    } else {
+                        // accumulator read: the next pair's layer 1 may now be followed by MMAs
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        ypart[(t * 2 + half) * BM + rl] = ysum;
+                        asm volatile("bar.sync 1, 256;" ::: "memory");
+                        const int64_t grow = (2 * pr + t) * BM + rl;
+                        if (half == 0 && grow < p.n_valid)
+                            p.y[grow] = ypart[(t * 2) * BM + rl] + ypart[(t * 2 + 1) * BM + rl] + b5;
+                    }
+                }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 9) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
-    }
-}
-
-// Layer 1 for inference, written in the tiled layout (k runs over the tiled order, so
-// consecutive threads write consecutive 2-byte words).
-__global__ void layer1_tiled_kernel(const float* __restrict__ x, int64_t n_valid, int64_t rows,
-                                    const float* __restrict__ p, __nv_bfloat16* __restrict__ a) {
-    // one thread per (row, 8-column chunk): work item k = (tile * 32 + chunk) * 128 + row % 128,
-    // so a warp writes 32 consecutive 16-byte words of the tiled layout
-    const int64_t total = rows * (H / 8);
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t tile = k / (BM * (H / 8));
-        const int rem = (int)(k % (BM * (H / 8)));
-        const int chunk = rem / BM;
-        const int64_t r = tile * BM + rem % BM;
-        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-        if (r < n_valid) {
-            x0 = x[r * 3 + 0];
-            x1 = x[r * 3 + 1];
-            x2 = x[r * 3 + 2];
-        }
-        uint32_t packed[4];
-#pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-            const int c = chunk * 8 + e;
-            float v0 = p[kOffB1 + c], v1 = p[kOffB1 + c + 1];
-            v0 = fmaf(p[kOffW1 + c * 3 + 0], x0, fmaf(p[kOffW1 + c * 3 + 1], x1, fmaf(p[kOffW1 + c * 3 + 2], x2, v0)));
-            v1 = fmaf(p[kOffW1 + c * 3 + 3], x0, fmaf(p[kOffW1 + c * 3 + 4], x1, fmaf(p[kOffW1 + c * 3 + 5], x2, v1)));
-            const __nv_bfloat162 b2 = __floats2bfloat162_rn(gelu(v0), gelu(v1));
-            packed[e >> 1] = *(const uint32_t*)&b2;
-        }
-        *(uint4*)(a + tile * (int64_t)(BM * H) + ((int64_t)chunk * BM + rem % BM) * 8) =
-            make_uint4(packed[0], packed[1], packed[2], packed[3]);
     }
 }
 
@@ -746,8 +831,6 @@ struct kg_mlp {
     __nv_bfloat16* w = nullptr;    // [3][H][H]
     __nv_bfloat16* wt = nullptr;   // [3][H][H]
     __nv_bfloat16* wtile = nullptr;   // [3][32][H][8] (tiled for the persistent kernel)
-    __nv_bfloat16* at_inf[2] = {nullptr, nullptr};   // tiled inference activations
-    int64_t inf_cap = 0;
     int* error = nullptr;
     double* loss = nullptr;
     int64_t step = 0;
@@ -891,60 +974,37 @@ kg_status mlp_forward(kg_mlp* m, int64_t n_valid, int64_t rows, bool train) {
 // Inference: layer 1 (CUDA cores, tiled output), layers 2-3 with the persistent tcgen05
 // kernel, layer 4 with the output layer fused into its epilogue.
 kg_status mlp_infer(kg_mlp* m, int64_t n_valid, int64_t rows) {
-    if (rows > m->inf_cap) {
-        for (auto& q : m->at_inf) {
-            if (q) cudaFree(q);
-            q = nullptr;
-        }
-        m->inf_cap = 0;
-        for (auto& q : m->at_inf)
-            if (cudaMalloc(&q, rows * H * sizeof(__nv_bfloat16)) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(KG_ENOMEM, "mlp: device allocation failed");
-            }
-        m->inf_cap = rows;
-    }
     static bool configured = false;
     if (!configured) {
-        KG_CUDA_TRY(cudaFuncSetAttribute(umma_persistent_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPSmem));
-        KG_CUDA_TRY(cudaFuncSetAttribute(umma_persistent_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPSmem));
+        KG_CUDA_TRY(cudaFuncSetAttribute(mlp_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem));
         configured = true;
     }
-    const int grid1 = std::max(1, std::min<int>(sm_count() * 8, (int)((rows * (H / 8) + 255) / 256)));
-    layer1_tiled_kernel<<<grid1, 256, 0, m->stream>>>(m->x, n_valid, rows, m->params, m->at_inf[0]);
-    KG_CUDA_TRY(cudaGetLastError());
-    m->launches++;
-    const int64_t n_tiles = rows / BM;
-    const int grid = (int)std::min<int64_t>(n_tiles, sm_count());
-    for (int l = 2; l <= 4; l++) {
-        PArgs pa{};
-        pa.a_tiled = m->at_inf[(l - 2) & 1];
-        pa.n_tiles = n_tiles;
-        pa.w_tiled = m->wtile + (int64_t)(l - 2) * H * H;
-        pa.bias = m->params + layer_b(l);
-        pa.out_tiled = l < 4 ? m->at_inf[(l - 1) & 1] : nullptr;
-        pa.w5 = m->params + kOffW5;
-        pa.b5 = m->params + kOffB5;
-        pa.y = m->y;
-        pa.n_valid = n_valid;
-        pa.error = m->error;
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (m->timing) {
-            KG_CUDA_TRY(cudaEventCreate(&e0));
-            KG_CUDA_TRY(cudaEventCreate(&e1));
-            KG_CUDA_TRY(cudaEventRecord(e0, m->stream));
-        }
-        if (l < 4) umma_persistent_kernel<false><<<grid, kPThreads, kPSmem, m->stream>>>(pa);
-        else umma_persistent_kernel<true><<<grid, kPThreads, kPSmem, m->stream>>>(pa);
-        KG_CUDA_TRY(cudaGetLastError());
-        if (m->timing) {
-            KG_CUDA_TRY(cudaEventRecord(e1, m->stream));
-            m->gemm_events.push_back({e0, e1});
-            m->gemm_flop += 2.0 * BM * BN * (double)H * (double)n_tiles;
-            m->gemm_launches++;
-        }
-        m->launches++;
+    FArgs fa{};
+    fa.x = m->x;
+    fa.n_valid = n_valid;
+    fa.n_tiles = rows / BM;
+    fa.params = m->params;
+    fa.w_tiled = m->wtile;
+    fa.y = m->y;
+    fa.error = m->error;
+    const int64_t n_pairs = (fa.n_tiles + 1) / 2;
+    const int grid = (int)std::min<int64_t>(n_pairs, sm_count());
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (m->timing) {
+        KG_CUDA_TRY(cudaEventCreate(&e0));
+        KG_CUDA_TRY(cudaEventCreate(&e1));
+        KG_CUDA_TRY(cudaEventRecord(e0, m->stream));
     }
+    mlp_fused_kernel<<<grid, kPThreads, kFSmem, m->stream>>>(fa);
+    KG_CUDA_TRY(cudaGetLastError());
+    if (m->timing) {
+        KG_CUDA_TRY(cudaEventRecord(e1, m->stream));
+        m->gemm_events.push_back({e0, e1});
+        // tensor-core work: the three 256 x 256 layers on every (padded) tile of every pair
+        m->gemm_flop += 3.0 * 2.0 * BM * BN * (double)H * (double)(2 * n_pairs);
+        m->gemm_launches++;
+    }
+    m->launches++;
     return KG_OK;
 }
 
@@ -1089,8 +1149,6 @@ void kg_mlp_destroy(kg_mlp* m) {
     if (!m) return;
     cudaStreamSynchronize(m->stream);
     mlp_free_batch(m);
-    for (auto q : m->at_inf)
-        if (q) cudaFree(q);
     if (m->params) cudaFree(m->params);
     if (m->error) cudaFree(m->error);
     delete m;
