@@ -27,8 +27,13 @@
 
 namespace kg {
 
+// Threads per block: 256 for the streaming, reduction and complex64 kernels; 512 for the
+// FP64 recursion kernels (measured on the 2.1M-site sheet: 98 against 102 us per KPM step;
+// the FP64 step at 42 registers runs two 512-thread blocks per SM, and capping it at 40
+// registers for a third block measured slower, 106 us; the complex64 step is faster with 256).
 constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+template <typename T>
+constexpr int kBlock = sizeof(T) == sizeof(double) ? 512 : 256;
 
 // --------------------------------------------------------------------------------
 // Inner-product accumulators
@@ -64,8 +69,9 @@ struct Acc<float> {
 // Deterministic: fixed shuffle tree, then a fixed-order sum over warps.
 // dst receives [R][NACC] doubles for this block.
 // --------------------------------------------------------------------------------
-template <int R, int NACC>
+template <int R, int NACC, int NT>
 __device__ __forceinline__ void block_reduce(double (&acc)[NACC], double* __restrict__ dst) {
+    constexpr int kWarps = NT / 32;
     __shared__ double sm[kWarps][32][NACC];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if constexpr (R < 32) {
@@ -153,15 +159,16 @@ __device__ __forceinline__ float2 mk<float>(float x, float y) { return make_floa
 // speed once the indices are prefetched.)
 
 template <typename T, int R, bool ONSITE, bool FIRST>
-__global__ void __launch_bounds__(kThreads) kpm_sym_kernel(DevH H, const vec2_t<T>* __restrict__ cur,
-                                                           const vec2_t<T>* prev, vec2_t<T>* out,
-                                                           double* __restrict__ partial) {
+__global__ void __launch_bounds__(kBlock<T>) kpm_sym_kernel(DevH H, const vec2_t<T>* __restrict__ cur,
+                                                            const vec2_t<T>* prev, vec2_t<T>* out,
+                                                            double* __restrict__ partial) {
+    constexpr int NT = kBlock<T>;
     const int64_t n_items = H.n * R;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int64_t stride = (int64_t)gridDim.x * NT;
     const int r = threadIdx.x & (R - 1);
     const T c = (T)(FIRST ? H.h : 2.0 * H.h);
     Acc<T> a0, a1;
-    int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    int64_t w = (int64_t)blockIdx.x * NT + threadIdx.x;
     Idx3 nid;
     if (w < n_items) nid = load_idx(H.idx, H.istride, w / R);
     for (; w < n_items; w += stride) {
@@ -181,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) kpm_sym_kernel(DevH H, const vec2_t<
         a1.add_prod(yi, g.x.y);
     }
     double acc[2] = {a0.value(), a1.value()};
-    block_reduce<R, 2>(acc, partial + (int64_t)blockIdx.x * R * 2);
+    block_reduce<R, 2, NT>(acc, partial + (int64_t)blockIdx.x * R * 2);
 }
 
 // --------------------------------------------------------------------------------
@@ -190,17 +197,18 @@ __global__ void __launch_bounds__(kThreads) kpm_sym_kernel(DevH H, const vec2_t<
 // First step: phi_1 = H~ phi_0 and partials (<L|phi_1>, <L|phi_0>).
 // --------------------------------------------------------------------------------
 template <typename T, int R, bool ONSITE, bool FIRST>
-__global__ void __launch_bounds__(kThreads) kpm_gen_kernel(DevH H, const vec2_t<T>* __restrict__ L,
+__global__ void __launch_bounds__(kBlock<T>) kpm_gen_kernel(DevH H, const vec2_t<T>* __restrict__ L,
                                                            const vec2_t<T>* __restrict__ cur,
                                                            const vec2_t<T>* prev, vec2_t<T>* out,
                                                            double* __restrict__ partial) {
     constexpr int NACC = FIRST ? 4 : 2;
+    constexpr int NT = kBlock<T>;
     const int64_t n_items = H.n * R;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int64_t stride = (int64_t)gridDim.x * NT;
     const int r = threadIdx.x & (R - 1);
     const T c = (T)(FIRST ? H.h : 2.0 * H.h);
     Acc<T> a[NACC];
-    int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    int64_t w = (int64_t)blockIdx.x * NT + threadIdx.x;
     Idx3 nid;
     if (w < n_items) nid = load_idx(H.idx, H.istride, w / R);
     for (; w < n_items; w += stride) {
@@ -230,7 +238,7 @@ __global__ void __launch_bounds__(kThreads) kpm_gen_kernel(DevH H, const vec2_t<
     double acc[NACC];
 #pragma unroll
     for (int q = 0; q < NACC; q++) acc[q] = a[q].value();
-    block_reduce<R, NACC>(acc, partial + (int64_t)blockIdx.x * R * NACC);
+    block_reduce<R, NACC, NT>(acc, partial + (int64_t)blockIdx.x * R * NACC);
 }
 
 // --------------------------------------------------------------------------------
@@ -290,7 +298,7 @@ __global__ void __launch_bounds__(kThreads) kpm_sym_pair_kernel(DevH H, const fl
         t1.add_prod(y.w, g.x.w);
     }
     double acc[4] = {s0.value(), s1.value(), t0.value(), t1.value()};
-    block_reduce<R2, 4>(acc, partial + (int64_t)blockIdx.x * R * 2);
+    block_reduce<R2, 4, kThreads>(acc, partial + (int64_t)blockIdx.x * R * 2);
 }
 
 template <int R, bool ONSITE, bool FIRST>
@@ -346,7 +354,7 @@ __global__ void __launch_bounds__(kThreads) kpm_gen_pair_kernel(DevH H, const fl
     double acc[2 * NACC];
 #pragma unroll
     for (int q = 0; q < 2 * NACC; q++) acc[q] = a[q].value();
-    block_reduce<R2, 2 * NACC>(acc, partial + (int64_t)blockIdx.x * R * NACC);
+    block_reduce<R2, 2 * NACC, kThreads>(acc, partial + (int64_t)blockIdx.x * R * NACC);
 }
 
 // --------------------------------------------------------------------------------
@@ -440,17 +448,17 @@ __device__ __forceinline__ void add_term(vec2_t<T>& a, bool odd, T cr, T ci, T y
 }
 
 template <typename T, int R, int NCH, bool XC, bool FIRST, bool ONSITE, bool YPAR, bool ODD>
-__global__ void __launch_bounds__(kThreads) evolve_kernel(DevH H, double j0d, double crd, double cid,
+__global__ void __launch_bounds__(kBlock<T>) evolve_kernel(DevH H, double j0d, double crd, double cid,
                                                           ChainsT<T> ch) {
     using V2 = vec2_t<T>;
     const int64_t n_items = H.n * R;
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int64_t stride = (int64_t)gridDim.x * kBlock<T>;
     const int r = threadIdx.x & (R - 1);
     const T c = (T)(FIRST ? H.h : 2.0 * H.h);
     const T cx = FIRST ? (T)1 : (T)2;
     const T j0 = (T)j0d, cr = (T)crd, ci = (T)cid;
     const bool q_into_0 = (ch.qacc == nullptr);
-    int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    int64_t w = (int64_t)blockIdx.x * kBlock<T> + threadIdx.x;
     Idx3 nid;
     if (w < n_items) nid = load_idx(H.idx, H.istride, w / R);
     for (; w < n_items; w += stride) {
@@ -494,17 +502,29 @@ __global__ void __launch_bounds__(kThreads) evolve_kernel(DevH H, double j0d, do
             }
             const T d0 = cx * (T)d0d, d1 = cx * (T)d1d, d2 = cx * (T)d2d;
             T qr, qi;
+            // transport along x: the bond to the adjacent chain is vertical, (X_n - X_m) = 0,
+            // so its term is dropped (d2 = 0); along y all three slots contribute
             if constexpr (FIRST) {
-                qr = fma(d0, gs.a.x, fma(d1, gs.b.x, d2 * gs.c.x));
-                qi = fma(d0, gs.a.y, fma(d1, gs.b.y, d2 * gs.c.y));
+                if constexpr (YPAR) {
+                    qr = fma(d0, gs.a.x, fma(d1, gs.b.x, d2 * gs.c.x));
+                    qi = fma(d0, gs.a.y, fma(d1, gs.b.y, d2 * gs.c.y));
+                } else {
+                    qr = fma(d0, gs.a.x, d1 * gs.b.x);
+                    qi = fma(d0, gs.a.y, d1 * gs.b.y);
+                }
             } else {
                 const Nbr<T> gq = gather_at<T, R>(id, n, r, ch.qcur);
                 V2 qz = mk<T>(0, 0);
                 if (ch.qprev) qz = ch.qprev[w];
                 qr = hop<T>(c, gq.a.x, gq.b.x, gq.c.x, e, gq.x.x, qz.x, ONSITE);
                 qi = hop<T>(c, gq.a.y, gq.b.y, gq.c.y, e, gq.x.y, qz.y, ONSITE);
-                qr = fma(d0, gs.a.x, fma(d1, gs.b.x, fma(d2, gs.c.x, qr)));
-                qi = fma(d0, gs.a.y, fma(d1, gs.b.y, fma(d2, gs.c.y, qi)));
+                if constexpr (YPAR) {
+                    qr = fma(d0, gs.a.x, fma(d1, gs.b.x, fma(d2, gs.c.x, qr)));
+                    qi = fma(d0, gs.a.y, fma(d1, gs.b.y, fma(d2, gs.c.y, qi)));
+                } else {
+                    qr = fma(d0, gs.a.x, fma(d1, gs.b.x, qr));
+                    qi = fma(d0, gs.a.y, fma(d1, gs.b.y, qi));
+                }
             }
             ch.qnxt[w] = mk<T>(qr, qi);
             if (q_into_0) {
@@ -582,7 +602,7 @@ __global__ void __launch_bounds__(kThreads) dot_kernel(int64_t n_items, const ve
         a1.add_prod(-l.y, x.x);
     }
     double acc[2] = {a0.value(), a1.value()};
-    block_reduce<R, 2>(acc, partial + (int64_t)blockIdx.x * R * 2);
+    block_reduce<R, 2, kThreads>(acc, partial + (int64_t)blockIdx.x * R * 2);
 }
 
 __global__ void reduce_dot_kernel(const double* __restrict__ part, int grid, int R, double2* out, int64_t r_stride) {
@@ -617,21 +637,21 @@ int stream_grid(int64_t n_items) {
 // capped by the work.  A partial second wave would leave most SMs idle at the end of
 // every launch (the DP pipe is the bottleneck, so the tail costs its full share).
 template <typename K>
-static int one_wave_grid(K kernel, int64_t n_items) {
+static int one_wave_grid(K kernel, int64_t n_items, int threads = kThreads) {
     static thread_local std::unordered_map<const void*, int> cache;
     int per_sm = 0;
     auto it = cache.find((const void*)kernel);
     if (it != cache.end()) {
         per_sm = it->second;
     } else {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
             per_sm < 1) {
             cudaGetLastError();
             per_sm = 1;
         }
         cache[(const void*)kernel] = per_sm;
     }
-    const int64_t need = (n_items + kThreads - 1) / kThreads;
+    const int64_t need = (n_items + threads - 1) / threads;
     const int64_t wave = (int64_t)sm_count() * per_sm;
     const int64_t g = need < wave ? need : wave;
     return (int)(g < 1 ? 1 : g);
@@ -672,7 +692,7 @@ cudaError_t launch_kpm_sym(const DevH& H, int R, bool first, const vec2_t<T>* cu
         }
     }
     KG_DISPATCH_R(R, KG_BOOL(ons, ON, KG_BOOL(first, FI,
-        kpm_sym_kernel<T, RR, ON, FI><<<grid, kThreads, 0, s>>>(H, cur, prev, out, partial))));
+        kpm_sym_kernel<T, RR, ON, FI><<<grid, kBlock<T>, 0, s>>>(H, cur, prev, out, partial))));
     return cudaGetLastError();
 }
 
@@ -693,7 +713,7 @@ cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const vec2_t<T>* L,
         }
     }
     KG_DISPATCH_R(R, KG_BOOL(ons, ON, KG_BOOL(first, FI,
-        kpm_gen_kernel<T, RR, ON, FI><<<grid, kThreads, 0, s>>>(H, L, cur, prev, out, partial))));
+        kpm_gen_kernel<T, RR, ON, FI><<<grid, kBlock<T>, 0, s>>>(H, L, cur, prev, out, partial))));
     return cudaGetLastError();
 }
 
@@ -726,7 +746,7 @@ int kpm_grid(const DevH& H, int R, bool sym) {
     }
     const int64_t items = H.n * R;
     int g = stream_grid(items);
-    auto pick = [&](auto k) { g = one_wave_grid(k, items); };
+    auto pick = [&](auto k) { g = one_wave_grid(k, items, kBlock<T>); };
     switch (R) {
 #define KG_KPM_GRID_CASE(RV)                                                                   \
         case RV:                                                                              \
@@ -768,8 +788,8 @@ static void evolve_dispatch(const DevH& H, bool first, double j0, double cr, dou
     const bool odd = first || cr == 0.0;   // the first step is the m = 1 term
     KG_BOOL(first, FI, KG_BOOL(ons, ON, KG_BOOL(ypar, YP, KG_BOOL(odd, OD,
         if constexpr (!FI || OD) {
-            const int g = one_wave_grid(evolve_kernel<T, R, NCH, XC, FI, ON, YP, OD>, H.n * R);
-            evolve_kernel<T, R, NCH, XC, FI, ON, YP, OD><<<g, kThreads, 0, s>>>(H, j0, cr, ci, ch);
+            const int g = one_wave_grid(evolve_kernel<T, R, NCH, XC, FI, ON, YP, OD>, H.n * R, kBlock<T>);
+            evolve_kernel<T, R, NCH, XC, FI, ON, YP, OD><<<g, kBlock<T>, 0, s>>>(H, j0, cr, ci, ch);
         }))));
 }
 
