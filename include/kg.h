@@ -154,6 +154,25 @@ kg_status kg_vac(kg_hamiltonian* h, const kg_run* run, const double* phi, double
  * phi: host or device [N][R][2].  mu_out: host or device [R][N_c][M][2]. */
 kg_status kg_msd(kg_hamiltonian* h, const kg_run* run, const double* phi, double* mu_out);
 
+/* Resumable time loops, for checkpointing long runs (the paper has no counterpart; its time
+ * loops, Algorithms 2-3, carry exactly this state from one t_m to the next).  Each call
+ * advances the loop state by run->n_times steps of run->dt and returns the moments at the
+ * n_times new times; chaining calls reproduces one long run bit for bit.
+ *   kg_msd_resume: state (psi, xi) = (U(t) phi, [X, U(t)] phi) (Eq. 44); xi NULL means a
+ *     fresh start at t = 0 (psi = phi, xi = 0).
+ *   kg_vac_resume: state (a, b) = (U^dagger(t) phi, U^dagger(t) V phi) (Eqs. 42-43); b NULL
+ *     means a fresh start (a = phi, b = V phi).
+ * psi, xi, a, b: host or device [N][R][2] complex128 (also for KG_C64, where the state is
+ * converted on the way in and out).  mu_out: host or device [R][N_c][M][2], the moments at
+ * t + dt .. t + N_c dt.  psi_out/xi_out (a_out/b_out): host or device [N][R][2], caller-owned,
+ * both or neither (NULL: the final state is not returned); they may be the input buffers.
+ * Every time loop checks that U(dt) kept the norm of psi (a): KG_ENUMERIC when it drifts by
+ * more than 1e-10 (FP64) or 1e-3 (KG_C64) relative, e.g. for a far too loose bessel_tol. */
+kg_status kg_msd_resume(kg_hamiltonian* h, const kg_run* run, const double* psi, const double* xi,
+                        double* mu_out, double* psi_out, double* xi_out);
+kg_status kg_vac_resume(kg_hamiltonian* h, const kg_run* run, const double* a, const double* b,
+                        double* mu_out, double* a_out, double* b_out);
+
 /* Fourier moments F_n = <phi|U(n dtau)|phi>, n = -N_m .. N_m (Eq. 25, Algorithm 4), with
  * the Nyquist step dtau = pi hbar for the scaled Hamiltonian (Sec. 4.2), i.e. U(dtau) =
  * exp(-i pi H~) applied n times forward and n times backward.  run->n_moments is N_m,
@@ -206,6 +225,11 @@ kg_status kg_batched_tuning(int* block_width, double* ms_per_step, int* n_ctas, 
 
 /* Frees the cached batch (its device memory and graphs). */
 kg_status kg_batched_release(void);
+
+/* Test hook for failure detection: every workspace allocation of a handle larger than
+ * `bytes` fails with KG_ENOMEM as if the device were out of memory (0 = no cap).  Injects
+ * allocation failures on the host; the handle stays usable once the cap is lifted. */
+kg_status kg_test_alloc_cap(uint64_t bytes);
 
 /* Test hook for failure detection: CTA `cta` of the cached batch stops publishing its
  * step flags after step 0, so its neighbours' bounded waits run out and the next

@@ -81,6 +81,9 @@ ABI = [
     ("kg_batched_tuning", _I, [_P, _P, _P, _I, _P, _P]),
     ("kg_batched_release", _I, []),
     ("kg_batched_test_stall", _I, [_I]),
+    ("kg_msd_resume", _I, [_P, ctypes.POINTER(_Run), _P, _P, _P, _P, _P]),
+    ("kg_vac_resume", _I, [_P, ctypes.POINTER(_Run), _P, _P, _P, _P, _P]),
+    ("kg_test_alloc_cap", _I, [ctypes.c_uint64]),
     ("kg_ftm_dos_moments", _I, [_P, ctypes.POINTER(_Run), _P, _P]),
     ("kg_ftm_sum", _I, [_P, _I, _I, _P, _I, _D, _D, _P]),
     ("kg_ballistic", _I, [_P, _P, _I, _I, _D, _D, _P, _P]),
@@ -285,6 +288,39 @@ def msd(h: Hamiltonian, phi, n_moments: int, n_times: int, dt: float, *, bessel_
     r = _nvec(phi, h.n)
     run = _run(n_moments, r, n_times, precision, dt, bessel_tol)
     return _moments_call(lib().kg_msd, h, phi, run, (r, n_times, n_moments), out)
+
+
+def _resume_call(fn, h: Hamiltonian, s0, s1, n_moments, n_times, dt, bessel_tol, precision):
+    r = _nvec(s0, h.n)
+    run = _run(n_moments, r, n_times, precision, dt, bessel_tol)
+    p0, k0 = _complex_in(s0)
+    p1, k1 = (_complex_in(s1) if s1 is not None else (0, None))
+    mu = np.zeros((r, n_times, n_moments), dtype=np.complex128)
+    o0 = np.zeros((h.n, r), dtype=np.complex128)
+    o1 = np.zeros((h.n, r), dtype=np.complex128)
+    _check(fn(h.handle, ctypes.byref(run), ctypes.c_void_p(p0), ctypes.c_void_p(p1 or None),
+              ctypes.c_void_p(mu.ctypes.data), ctypes.c_void_p(o0.ctypes.data), ctypes.c_void_p(o1.ctypes.data)))
+    squeeze = len(s0.shape) == 1
+    return mu, (o0[:, 0] if squeeze else o0), (o1[:, 0] if squeeze else o1)
+
+
+def msd_resume(h: Hamiltonian, psi, xi, n_moments: int, n_times: int, dt: float, *, bessel_tol=1e-15,
+               precision: int = KG_FP64):
+    """kg_msd_resume: advance (psi, xi) by n_times steps (xi None = fresh start) ->
+    (moments [R][n_times][M] at the new times, psi', xi')."""
+    return _resume_call(lib().kg_msd_resume, h, psi, xi, n_moments, n_times, dt, bessel_tol, precision)
+
+
+def vac_resume(h: Hamiltonian, a, b, n_moments: int, n_times: int, dt: float, *, bessel_tol=1e-15,
+               precision: int = KG_FP64):
+    """kg_vac_resume: advance (A, B) by n_times steps (b None = fresh start, B = V A) ->
+    (moments [R][n_times][M] at the new times, A', B')."""
+    return _resume_call(lib().kg_vac_resume, h, a, b, n_moments, n_times, dt, bessel_tol, precision)
+
+
+def test_alloc_cap(n_bytes: int):
+    """kg_test_alloc_cap: workspace allocations above n_bytes fail with KG_ENOMEM (0 = off)."""
+    _check(lib().kg_test_alloc_cap(int(n_bytes)))
 
 
 def ftm_dos_moments(h: Hamiltonian, phi, n_m: int, *, bessel_tol=1e-15, out=None):

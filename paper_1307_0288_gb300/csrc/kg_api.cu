@@ -2,6 +2,8 @@
 // time-evolution drivers (Algorithms 2, 3, 5, 6, 7 of the paper).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -11,6 +13,10 @@
 #include "kg_internal.h"
 
 namespace kg {
+
+// Test hook: workspace allocations above this many bytes fail as if the device were out
+// of memory (0 = no cap).  Injects KG_ENOMEM on the host, without a real allocation failure.
+static std::atomic<unsigned long long> g_alloc_cap{0};
 
 // Device buffer owned by the handle.
 struct DevBuf {
@@ -25,6 +31,9 @@ struct DevBuf {
     // vector block relies on it).
     kg_status ensure(size_t want, cudaStream_t s) {
         if (bytes >= want) return KG_OK;
+        const unsigned long long cap = g_alloc_cap.load();
+        if (cap && want > cap)
+            return fail(KG_ENOMEM, "workspace allocation of " + std::to_string(want) + " bytes exceeds the test cap");
         release();
         if (cudaMalloc(&p, want) != cudaSuccess) {
             cudaGetLastError();
@@ -55,7 +64,7 @@ struct kg_hamiltonian {
     // workspace
     static constexpr int kNumVec = 10;
     kg::DevBuf vec[kNumVec];
-    kg::DevBuf part_first, part_ring, moments, flag;
+    kg::DevBuf part_first, part_ring, moments, flag, norms, norm_part;
     // timing
     bool timing = false;
     std::vector<kg::TimedPhase> phases;
@@ -371,20 +380,82 @@ static kg_status dos_impl(kg_hamiltonian* h, int R, int M, const double* phi) {
                           (double2*)h->moments.p, M);
 }
 
+// ||x_r||^2 of the R vectors of a block into norms[slot][r].x (device).
 template <typename T>
-static kg_status vac_impl(kg_hamiltonian* h, int R, int M, int NC, const Series& ser, const double* phi) {
+static kg_status block_norms(kg_hamiltonian* h, int R, const vec2_t<T>* x, int slot) {
+    const int grid = stream_grid(h->n * R);
+    KG_TRY(h->norm_part.ensure((size_t)grid * R * 2 * sizeof(double), h->stream));
+    KG_CUDA_TRY(launch_dot<T>(h->n * R, R, x, x, (double*)h->norm_part.p, grid,
+                              (double2*)h->norms.p + (size_t)slot * R, 1, h->stream));
+    h->counters.other_launches += 2;
+    return KG_OK;
+}
+
+// U(dt) is unitary (Eq. 36): the norm of the evolved vector must not drift.  Fails with
+// KG_ENUMERIC when any of the `slots` recorded norms differs from slot 0 by more than
+// 1e-10 (FP64) or 1e-3 (complex64) relative, e.g. for a Bessel truncation far too loose.
+template <typename T>
+static kg_status check_norms(kg_hamiltonian* h, int R, int slots) {
+    std::vector<double2> nrm((size_t)slots * R);
+    KG_CUDA_TRY(cudaMemcpyAsync(nrm.data(), h->norms.p, nrm.size() * sizeof(double2), cudaMemcpyDeviceToHost,
+                                h->stream));
+    KG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const double tol = sizeof(T) == sizeof(double) ? 1e-10 : 1e-3;
+    for (int r = 0; r < R; r++) {
+        const double n0 = nrm[(size_t)r].x;
+        for (int t = 1; t < slots; t++) {
+            const double nt = nrm[(size_t)t * R + r].x;
+            if (!std::isfinite(nt) || std::fabs(nt - n0) > tol * std::max(n0, 1e-300))
+                return fail(KG_ENUMERIC, "norm drift of the evolved vector " + std::to_string(r) + ": |phi|^2 " +
+                                             std::to_string(n0) + " -> " + std::to_string(nt) + " after " +
+                                             std::to_string(t) + " steps (U(dt) must be unitary; bessel_tol?)");
+        }
+    }
+    return KG_OK;
+}
+
+// Writes block `src` (precision T) to the caller's complex128 buffer (host or device);
+// complex64 goes through the scratch block `tmp`.
+template <typename T>
+static kg_status state_out(kg_hamiltonian* h, int R, const vec2_t<T>* src, int tmp, double* dst) {
+    const size_t bytes = (size_t)h->n * R * sizeof(double2);
+    const void* from = src;
+    if constexpr (sizeof(T) != sizeof(double)) {
+        KG_CUDA_TRY(launch_to_c128(src, V(h, tmp), h->n * R, h->stream));
+        h->counters.other_launches += 1;
+        from = V(h, tmp);
+    }
+    KG_CUDA_TRY(cudaMemcpyAsync(dst, from, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                h->stream));
+    return KG_OK;
+}
+
+// VAC time loop (Algorithm 2, Eqs. 42-43) on the state (A, B), A = U^dagger(t) phi,
+// B = U^dagger(t) V phi.  Fresh run (resume = false): A = phi, B = V phi, moments at
+// t_0 .. t_{NC-1}.  Resume: the state (a_in, b_in; b_in null means V a_in) is advanced NC
+// steps, with the moments after each step; the final state goes to (a_out, b_out) if given.
+template <typename T>
+static kg_status vac_impl(kg_hamiltonian* h, int R, int M, int NC, const Series& ser, const double* a_in,
+                          const double* b_in, bool resume, double* a_out, double* b_out) {
     using V2 = vec2_t<T>;
     // blocks: 0 A, 1 B, 2 A', 3 B', 4 L, 5 p1(A), 6 p1(B), 7 kpm b0, 8 kpm b1
     KG_TRY(ensure_vectors(h, R, 9));
     V2 *A = VT<T>(h, 0), *B = VT<T>(h, 1), *A2 = VT<T>(h, 2), *B2 = VT<T>(h, 3), *L = VT<T>(h, 4);
     const double vscale = h->emax / kHbarEvFs;
-    KG_TRY(stage_input<T>(h, phi, R, 0, 7));
+    KG_TRY(stage_input<T>(h, a_in, R, 0, 7));
+    if (b_in) KG_TRY(stage_input<T>(h, b_in, R, 1, 7));
     KG_TRY(clear_zero_rows<T>(h, R, 9));   // after staging: it writes complex128 rows into block 7
-    KG_CUDA_TRY(launch_apply<T>(h->dev, R, 2, vscale, A, B, h->stream));   // B = V phi
-    h->counters.other_launches += 1;
+    if (!b_in) {
+        KG_CUDA_TRY(launch_apply<T>(h->dev, R, 2, vscale, A, B, h->stream));   // B = V phi
+        h->counters.other_launches += 1;
+    }
+    const int steps = resume ? NC : NC - 1;
+    KG_TRY(h->norms.ensure((size_t)(steps + 1) * R * sizeof(double2), h->stream));
+    KG_TRY(block_norms<T>(h, R, A, 0));
     double2* mu = (double2*)h->moments.p;
+    int slot = 0;
     for (int t = 0; t < NC; t++) {
-        if (t > 0) {
+        if (t > 0 || resume) {
             // A <- U(-dt) A, B <- U(-dt) B  (Eqs. 42-43)
             V2* in[2] = {A, B};
             V2* p1[2] = {VT<T>(h, 5), VT<T>(h, 6)};
@@ -392,27 +463,40 @@ static kg_status vac_impl(kg_hamiltonian* h, int R, int M, int NC, const Series&
             KG_TRY(run_series<T>(h, R, ser, +1, 2, false, in, p1, acc, nullptr, nullptr, nullptr));
             std::swap(A, A2);
             std::swap(B, B2);
+            KG_TRY(block_norms<T>(h, R, A, ++slot));
         }
         KG_CUDA_TRY(launch_apply<T>(h->dev, R, 2, vscale, A, L, h->stream));   // L = V A
         h->counters.other_launches += 1;
         KG_TRY(kpm_moments<T>(h, R, M, false, L, B, VT<T>(h, 7), VT<T>(h, 8), mu + (int64_t)t * M,
                               (int64_t)NC * M));
     }
+    KG_TRY(check_norms<T>(h, R, slot + 1));
+    if (a_out) KG_TRY(state_out<T>(h, R, A, 7, a_out));
+    if (b_out) KG_TRY(state_out<T>(h, R, B, 8, b_out));
     return KG_OK;
 }
 
+// MSD time loop (Algorithm 3, Eq. 44) on the state (psi, xi), psi = U(t) phi,
+// xi = [X, U(t)] phi.  Fresh run: psi = phi, xi = 0, moments at t_0 (zero) .. t_{NC-1}.
+// Resume: the state (psi_in, xi_in; xi_in null means 0) is advanced NC steps, with the
+// moments after each step; the final state goes to (psi_out, xi_out) if given.
 template <typename T>
-static kg_status msd_impl(kg_hamiltonian* h, int R, int M, int NC, const Series& ser, const double* phi) {
+static kg_status msd_impl(kg_hamiltonian* h, int R, int M, int NC, const Series& ser, const double* psi_in,
+                          const double* xi_in, bool resume, double* psi_out, double* xi_out) {
     using V2 = vec2_t<T>;
     // blocks: 0 psi, 1 xi, 2 psi', 3 xi', 4 p1(xi), 5 p1(psi), 6 q1, 7 q0
     KG_TRY(ensure_vectors(h, R, 8));
     V2 *psi = VT<T>(h, 0), *xi = VT<T>(h, 1), *psi2 = VT<T>(h, 2), *xi2 = VT<T>(h, 3);
-    KG_TRY(stage_input<T>(h, phi, R, 0, 7));
+    KG_TRY(stage_input<T>(h, psi_in, R, 0, 7));
+    if (xi_in) KG_TRY(stage_input<T>(h, xi_in, R, 1, 7));
     KG_TRY(clear_zero_rows<T>(h, R, 8));   // after staging: it writes complex128 rows into block 7
-    KG_CUDA_TRY(cudaMemsetAsync(xi, 0, vec_bytes(h, R), h->stream));   // [X, U(0)] = 0
+    if (!xi_in) KG_CUDA_TRY(cudaMemsetAsync(xi, 0, vec_bytes(h, R), h->stream));   // [X, U(0)] = 0
     double2* mu = (double2*)h->moments.p;
-    KG_CUDA_TRY(cudaMemsetAsync(mu, 0, (size_t)R * NC * M * sizeof(double2), h->stream));
-    for (int t = 1; t < NC; t++) {
+    const int t0 = resume ? 0 : 1;
+    if (!resume) KG_CUDA_TRY(cudaMemsetAsync(mu, 0, (size_t)R * NC * M * sizeof(double2), h->stream));
+    KG_TRY(h->norms.ensure((size_t)(NC - t0 + 1) * R * sizeof(double2), h->stream));
+    KG_TRY(block_norms<T>(h, R, psi, 0));
+    for (int t = t0; t < NC; t++) {
         // xi <- U(dt) xi + [X, U(dt)] psi ;  psi <- U(dt) psi  (Eq. 44)
         V2* in[2] = {xi, psi};
         V2* p1[2] = {VT<T>(h, 4), VT<T>(h, 5)};
@@ -420,10 +504,14 @@ static kg_status msd_impl(kg_hamiltonian* h, int R, int M, int NC, const Series&
         KG_TRY(run_series<T>(h, R, ser, -1, 2, true, in, p1, acc, VT<T>(h, 6), VT<T>(h, 7), nullptr));
         std::swap(xi, xi2);
         std::swap(psi, psi2);
+        KG_TRY(block_norms<T>(h, R, psi, t - t0 + 1));
         // moments of xi; scratch: the now-free chain buffers 4 and 5
         KG_TRY(kpm_moments<T>(h, R, M, true, xi, xi, VT<T>(h, 4), VT<T>(h, 5), mu + (int64_t)t * M,
                               (int64_t)NC * M));
     }
+    KG_TRY(check_norms<T>(h, R, NC - t0 + 1));
+    if (psi_out) KG_TRY(state_out<T>(h, R, psi, 6, psi_out));
+    if (xi_out) KG_TRY(state_out<T>(h, R, xi, 7, xi_out));
     return KG_OK;
 }
 
@@ -548,6 +636,8 @@ void kg_destroy_hamiltonian(kg_hamiltonian* h) {
     h->part_ring.release();
     h->moments.release();
     h->flag.release();
+    h->norms.release();
+    h->norm_part.release();
     for (auto& p : h->phases) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -578,8 +668,8 @@ kg_status kg_vac(kg_hamiltonian* h, const kg_run* run, const double* phi, double
     Series ser;
     if (NC > 1) KG_TRY(series_for(h, run->dt, run->bessel_tol, &ser));
     KG_TRY(ensure_moments(h, (size_t)R * NC * M));
-    if (run->precision == KG_C64) KG_TRY(vac_impl<float>(h, R, M, NC, ser, phi));
-    else KG_TRY(vac_impl<double>(h, R, M, NC, ser, phi));
+    if (run->precision == KG_C64) KG_TRY(vac_impl<float>(h, R, M, NC, ser, phi, nullptr, false, nullptr, nullptr));
+    else KG_TRY(vac_impl<double>(h, R, M, NC, ser, phi, nullptr, false, nullptr, nullptr));
     KG_TRY(check_finite(h, h->moments.p, (size_t)R * NC * M * 2));
     return copy_out(h, h->moments.p, mu_out, (size_t)R * NC * M * sizeof(double2));
 }
@@ -593,10 +683,50 @@ kg_status kg_msd(kg_hamiltonian* h, const kg_run* run, const double* phi, double
     Series ser;
     if (NC > 1) KG_TRY(series_for(h, run->dt, run->bessel_tol, &ser));
     KG_TRY(ensure_moments(h, (size_t)R * NC * M));
-    if (run->precision == KG_C64) KG_TRY(msd_impl<float>(h, R, M, NC, ser, phi));
-    else KG_TRY(msd_impl<double>(h, R, M, NC, ser, phi));
+    if (run->precision == KG_C64) KG_TRY(msd_impl<float>(h, R, M, NC, ser, phi, nullptr, false, nullptr, nullptr));
+    else KG_TRY(msd_impl<double>(h, R, M, NC, ser, phi, nullptr, false, nullptr, nullptr));
     KG_TRY(check_finite(h, h->moments.p, (size_t)R * NC * M * 2));
     return copy_out(h, h->moments.p, mu_out, (size_t)R * NC * M * sizeof(double2));
+}
+
+kg_status kg_vac_resume(kg_hamiltonian* h, const kg_run* run, const double* a, const double* b, double* mu_out,
+                        double* a_out, double* b_out) {
+    clear_error();
+    KG_TRY(check_run(h, run, true));
+    if (!a || !mu_out) return fail(KG_EINVAL, "a and mu_out must not be NULL");
+    if ((a_out == nullptr) != (b_out == nullptr)) return fail(KG_EINVAL, "a_out and b_out go together");
+    KG_TRY(check_device(h));
+    const int R = run->n_vectors, M = run->n_moments, NC = run->n_times;
+    Series ser;
+    KG_TRY(series_for(h, run->dt, run->bessel_tol, &ser));
+    KG_TRY(ensure_moments(h, (size_t)R * NC * M));
+    if (run->precision == KG_C64) KG_TRY(vac_impl<float>(h, R, M, NC, ser, a, b, true, a_out, b_out));
+    else KG_TRY(vac_impl<double>(h, R, M, NC, ser, a, b, true, a_out, b_out));
+    KG_TRY(check_finite(h, h->moments.p, (size_t)R * NC * M * 2));
+    return copy_out(h, h->moments.p, mu_out, (size_t)R * NC * M * sizeof(double2));
+}
+
+kg_status kg_msd_resume(kg_hamiltonian* h, const kg_run* run, const double* psi, const double* xi, double* mu_out,
+                        double* psi_out, double* xi_out) {
+    clear_error();
+    KG_TRY(check_run(h, run, true));
+    if (!psi || !mu_out) return fail(KG_EINVAL, "psi and mu_out must not be NULL");
+    if ((psi_out == nullptr) != (xi_out == nullptr)) return fail(KG_EINVAL, "psi_out and xi_out go together");
+    KG_TRY(check_device(h));
+    const int R = run->n_vectors, M = run->n_moments, NC = run->n_times;
+    Series ser;
+    KG_TRY(series_for(h, run->dt, run->bessel_tol, &ser));
+    KG_TRY(ensure_moments(h, (size_t)R * NC * M));
+    if (run->precision == KG_C64) KG_TRY(msd_impl<float>(h, R, M, NC, ser, psi, xi, true, psi_out, xi_out));
+    else KG_TRY(msd_impl<double>(h, R, M, NC, ser, psi, xi, true, psi_out, xi_out));
+    KG_TRY(check_finite(h, h->moments.p, (size_t)R * NC * M * 2));
+    return copy_out(h, h->moments.p, mu_out, (size_t)R * NC * M * sizeof(double2));
+}
+
+kg_status kg_test_alloc_cap(uint64_t bytes) {
+    clear_error();
+    g_alloc_cap.store(bytes);
+    return KG_OK;
 }
 
 kg_status kg_ftm_dos_moments(kg_hamiltonian* h, const kg_run* run, const double* phi, double* f_out) {

@@ -36,7 +36,7 @@
 
 namespace kg {
 
-constexpr int kBThreads = 256;
+constexpr int kBThreads = 512;   // measured on the 16-ribbon batch: 7.05 against 7.19 ms per step with 256
 constexpr int kBWarps = kBThreads / 32;
 constexpr long long kSpinLimit = 1ll << 22;   // polls of ~100 ns before giving up
 

@@ -152,6 +152,7 @@ cudaError_t launch_dot(int64_t n_items, int R, const vec2_t<T>* L, const vec2_t<
 
 // complex128 -> complex64, element-wise.
 cudaError_t launch_to_c64(const double2* in, float2* out, int64_t n_items, cudaStream_t s);
+cudaError_t launch_to_c128(const float2* in, double2* out, int64_t n_items, cudaStream_t s);
 
 // Grid size (CTAs) for a streaming kernel over n_items = n * R complex items.
 int stream_grid(int64_t n_items);

@@ -827,6 +827,19 @@ cudaError_t launch_dot(int64_t n_items, int R, const vec2_t<T>* L, const vec2_t<
     return cudaGetLastError();
 }
 
+__global__ void to_c128_kernel(const float2* __restrict__ in, double2* __restrict__ out, int64_t n_items) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_items; k += stride) {
+        const float2 v = in[k];
+        out[k] = make_double2((double)v.x, (double)v.y);
+    }
+}
+
+cudaError_t launch_to_c128(const float2* in, double2* out, int64_t n_items, cudaStream_t s) {
+    to_c128_kernel<<<stream_grid(n_items), kThreads, 0, s>>>(in, out, n_items);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_to_c64(const double2* in, float2* out, int64_t n_items, cudaStream_t s) {
     to_c64_kernel<<<stream_grid(n_items), kThreads, 0, s>>>(in, out, n_items);
     return cudaGetLastError();
