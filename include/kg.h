@@ -209,7 +209,8 @@ kg_status kg_evolve(kg_hamiltonian* h, double dt, int which, double bessel_tol,
  * that hold its sites' neighbours; the call's device work is captured once in a CUDA
  * graph and replayed.  The block width (vectors per thread group: 8..64) is chosen by a
  * measured autotuner on the first call for a given member set and R.
- *   hs       n_h member handles (the batch is cached for the same list and R).
+ *   hs       n_h member handles (one batch is cached per process for the same list and R;
+ *            calls must not run concurrently from several host threads).
  *   run      n_moments M, n_vectors R (power of two <= 64), precision KG_FP64.
  *   phis     n_h pointers, host or device, member i's vectors [N_i][R][2].
  *   mu_out   host or device [n_h][R][M][2].

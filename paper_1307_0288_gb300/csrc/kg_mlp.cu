@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -140,6 +141,20 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
                  "r"(v.w)
                  : "memory");
+}
+
+// The dynamic shared memory limit is a per-device function attribute: set it once per
+// (kernel, device), the devices done kept as bits of `done`.
+template <typename K>
+static kg_status set_smem_once(K kernel, int bytes, std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    KG_CUDA_TRY(cudaGetDevice(&dev));
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(done.load() & bit)) {
+        KG_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        done.fetch_or(bit);
+    }
+    return KG_OK;
 }
 
 #define KG_TMEM_LD32(taddr, v)                                                                       \
@@ -919,12 +934,8 @@ bool is_dev(const void* p) {
 
 template <int EPI>
 kg_status launch_gemm(kg_mlp* m, const GemmArgs& g, int64_t m_tiles, int splits) {
-    static bool configured = false;
-    if (!configured) {
-        KG_CUDA_TRY(cudaFuncSetAttribute(umma_gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kGemmSmem));
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{0};
+    KG_TRY(set_smem_once(umma_gemm_kernel<EPI>, kGemmSmem, configured));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (m->timing) {
         KG_CUDA_TRY(cudaEventCreate(&e0));
@@ -974,11 +985,8 @@ kg_status mlp_forward(kg_mlp* m, int64_t n_valid, int64_t rows, bool train) {
 // Inference: layer 1 (CUDA cores, tiled output), layers 2-3 with the persistent tcgen05
 // kernel, layer 4 with the output layer fused into its epilogue.
 kg_status mlp_infer(kg_mlp* m, int64_t n_valid, int64_t rows) {
-    static bool configured = false;
-    if (!configured) {
-        KG_CUDA_TRY(cudaFuncSetAttribute(mlp_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem));
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{0};
+    KG_TRY(set_smem_once(mlp_fused_kernel, kFSmem, configured));
     FArgs fa{};
     fa.x = m->x;
     fa.n_valid = n_valid;
