@@ -219,10 +219,13 @@ kg_status kg_evolve(kg_hamiltonian* h, double dt, int which, double bessel_tol,
 kg_status kg_batched_dos_moments(kg_hamiltonian* const* hs, int n_h, const kg_run* run,
                                  const double* const* phis, double* mu_out);
 
-/* Result of the autotuner for the cached batch: chosen block width, its time per
- * recursion step (ms), the CTA count, and up to max_log measured (width, ms) pairs. */
+/* Result of the autotuner for the cached batch.  It measures every (block width, CTA
+ * budget) pair: widths 8..64 (vectors one thread group covers per pass) and a budget of one
+ * occupancy wave of CTAs or half of one (the tile schedule: how many site ranges the
+ * members are cut into).  Returns the chosen width, its time per recursion step (ms) and
+ * CTA count, and up to max_log measured trials (width, CTAs, ms per step). */
 kg_status kg_batched_tuning(int* block_width, double* ms_per_step, int* n_ctas, int max_log,
-                            int* log_width, double* log_ms);
+                            int* log_width, int* log_ctas, double* log_ms);
 
 /* Frees the cached batch (its device memory and graphs). */
 kg_status kg_batched_release(void);

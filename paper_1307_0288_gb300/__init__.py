@@ -78,7 +78,7 @@ ABI = [
     ("kg_conductivity", _I, [_I, _P, _I, _I, _D, _P]),
     ("kg_dos_moments_noalloc", _I, [_P, _P, _I64, _D, _I, _I, _P, _P, _P]),
     ("kg_batched_dos_moments", _I, [_P, _I, ctypes.POINTER(_Run), _P, _P]),
-    ("kg_batched_tuning", _I, [_P, _P, _P, _I, _P, _P]),
+    ("kg_batched_tuning", _I, [_P, _P, _P, _I, _P, _P, _P]),
     ("kg_batched_release", _I, []),
     ("kg_batched_test_stall", _I, [_I]),
     ("kg_msd_resume", _I, [_P, ctypes.POINTER(_Run), _P, _P, _P, _P, _P]),
@@ -404,10 +404,11 @@ def batched_tuning() -> dict:
     """kg_batched_tuning: the autotuner's choice and its measurements."""
     bw, nc = ctypes.c_int(), ctypes.c_int()
     ms = ctypes.c_double()
-    lw = (ctypes.c_int * 8)()
-    lm = (ctypes.c_double * 8)()
-    _check(lib().kg_batched_tuning(ctypes.byref(bw), ctypes.byref(ms), ctypes.byref(nc), 8, lw, lm))
-    log = [(lw[k], lm[k]) for k in range(8) if lw[k]]
+    lw = (ctypes.c_int * 16)()
+    lc = (ctypes.c_int * 16)()
+    lm = (ctypes.c_double * 16)()
+    _check(lib().kg_batched_tuning(ctypes.byref(bw), ctypes.byref(ms), ctypes.byref(nc), 16, lw, lc, lm))
+    log = [(lw[k], lc[k], lm[k]) for k in range(16) if lw[k]]
     return {"block_width": bw.value, "ms_per_step": ms.value, "n_ctas": nc.value, "log": log}
 
 

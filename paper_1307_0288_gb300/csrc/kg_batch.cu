@@ -289,11 +289,17 @@ struct Batch {
         int* inst_c1 = nullptr;
         void* mem = nullptr;
     };
-    std::map<int, Sched> sched;
-    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (RB, M) -> graph
-    int tuned_rb = 0;
+    // A tuning configuration is (block width RB, CTA budget = one occupancy wave / split),
+    // encoded as cfg = RB * 8 + split.
+    std::map<int, Sched> sched;                                 // cfg -> schedule
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (cfg, M) -> graph
+    int tuned_cfg = 0;
     double tuned_ms_per_step = 0.0;
-    std::vector<std::pair<int, double>> tuning_log;
+    struct Trial {
+        int rb, n_cta;
+        double ms;
+    };
+    std::vector<Trial> tuning_log;
     int stall_cta = -1;   // test hook
     ~Batch() {
         for (auto& g : graphs) cudaGraphExecDestroy(g.second);
@@ -313,13 +319,15 @@ static kg_status member_table(const kg_hamiltonian* h, std::vector<int32_t>* out
     return KG_OK;
 }
 
-static kg_status build_schedule(Batch* b, int rb, Batch::Sched* s) {
+static kg_status build_schedule(Batch* b, int rb, int split, Batch::Sched* s) {
     int per_sm = 0;
     KG_BATCH_DISPATCH(b->R, rb, per_sm = batched_occupancy<R, RB>(b->onsite));
     if (per_sm < 1) return fail(KG_EINVAL, "batched: no kernel for this (R, block width)");
     const int n_inst = (int)b->members.size();
     const int64_t wave = (int64_t)sm_count() * per_sm;
-    int64_t budget = std::max<int64_t>(wave, n_inst);
+    // CTA budget: one occupancy wave (split 1) or a fraction of it (fewer, longer site
+    // ranges: fewer step flags to wait on, less parallelism); never below one per member
+    int64_t budget = std::max<int64_t>(wave / std::max(split, 1), n_inst);
     if (budget > wave) return fail(KG_EINVAL, "batched: more instances than co-resident CTAs");
     // CTAs per instance in proportion to its sites, at least one, at most one per 32 sites
     std::vector<int64_t> k(n_inst, 1);
@@ -488,24 +496,25 @@ static kg_status ensure_batch_buffers(Batch* b, int steps, int M) {
     return KG_OK;
 }
 
-static kg_status get_sched(Batch* b, int rb, Batch::Sched** out) {
-    auto it = b->sched.find(rb);
+static kg_status get_sched(Batch* b, int cfg, Batch::Sched** out) {
+    auto it = b->sched.find(cfg);
     if (it == b->sched.end()) {
         Batch::Sched s;
-        KG_TRY(build_schedule(b, rb, &s));
-        it = b->sched.emplace(rb, s).first;
+        KG_TRY(build_schedule(b, cfg / 8, cfg % 8, &s));
+        it = b->sched.emplace(cfg, s).first;
     }
     *out = &it->second;
     return KG_OK;
 }
 
 // Enqueues (and on first use captures into a graph) the device work for M moments.
-static kg_status run_graph(Batch* b, int rb, int M) {
+static kg_status run_graph(Batch* b, int cfg, int M) {
+    const int rb = cfg / 8;
     Batch::Sched* s = nullptr;
-    KG_TRY(get_sched(b, rb, &s));
+    KG_TRY(get_sched(b, cfg, &s));
     const int steps = std::max(1, (M + 1) / 2);   // step n yields moments 2n and 2n+1
     KG_TRY(ensure_batch_buffers(b, steps, M));
-    const auto key = std::make_pair(rb, M);
+    const auto key = std::make_pair(cfg, M);
     auto it = b->graphs.find(key);
     const bool direct = b->stall_cta >= 0;   // test hook runs are never cached as graphs
     if (it == b->graphs.end() || direct) {
@@ -579,31 +588,33 @@ static std::vector<int> candidate_widths(int R) {
 
 // Measures every block width on a short run (same batch, 24 moments) and keeps the fastest.
 static kg_status autotune(Batch* b) {
-    if (b->tuned_rb) return KG_OK;
+    if (b->tuned_cfg) return KG_OK;
     const int probe_m = 24;
     cudaEvent_t e0, e1;
     KG_CUDA_TRY(cudaEventCreate(&e0));
     KG_CUDA_TRY(cudaEventCreate(&e1));
     double best = 1e300;
-    int best_rb = 0;
-    for (int rb : candidate_widths(b->R)) {
-        KG_TRY(run_graph(b, rb, probe_m));   // warm-up and capture
-        KG_CUDA_TRY(cudaEventRecord(e0, b->stream));
-        for (int k = 0; k < 3; k++) KG_TRY(run_graph(b, rb, probe_m));
-        KG_CUDA_TRY(cudaEventRecord(e1, b->stream));
-        KG_TRY(check_error_flag(b));
-        float ms = 0;
-        KG_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-        const double per_step = ms / 3.0 / (probe_m / 2);
-        b->tuning_log.push_back({rb, per_step});
-        if (per_step < best) {
-            best = per_step;
-            best_rb = rb;
+    int best_cfg = 0;
+    for (int rb : candidate_widths(b->R))
+        for (int split : {1, 2}) {
+            const int cfg = rb * 8 + split;
+            KG_TRY(run_graph(b, cfg, probe_m));   // warm-up and capture
+            KG_CUDA_TRY(cudaEventRecord(e0, b->stream));
+            for (int k = 0; k < 3; k++) KG_TRY(run_graph(b, cfg, probe_m));
+            KG_CUDA_TRY(cudaEventRecord(e1, b->stream));
+            KG_TRY(check_error_flag(b));
+            float ms = 0;
+            KG_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            const double per_step = ms / 3.0 / (probe_m / 2);
+            b->tuning_log.push_back({rb, b->sched[cfg].n_cta, per_step});
+            if (per_step < best) {
+                best = per_step;
+                best_cfg = cfg;
+            }
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->tuned_rb = best_rb;
+    b->tuned_cfg = best_cfg;
     b->tuned_ms_per_step = best;
     return KG_OK;
 }
@@ -665,7 +676,7 @@ kg_status kg_batched_dos_moments(kg_hamiltonian* const* hs, int n_h, const kg_ru
                                     cudaMemcpyDefault, b->stream));
     KG_CUDA_TRY(cudaMemsetAsync(b->A + b->n_total * R, 0, (size_t)R * sizeof(double2), b->stream));
     KG_CUDA_TRY(cudaMemsetAsync(b->B + b->n_total * R, 0, (size_t)R * sizeof(double2), b->stream));
-    KG_TRY(run_graph(b, b->tuned_rb, M));
+    KG_TRY(run_graph(b, b->tuned_cfg, M));
     KG_TRY(check_error_flag(b));
     // error[1]: non-finite moments (cleared with the wait flags by every graph replay)
     KG_CUDA_TRY(launch_nonfinite((const double*)b->mu, (int64_t)n_h * R * M * 2, b->error + 1, b->stream));
@@ -681,14 +692,16 @@ kg_status kg_batched_dos_moments(kg_hamiltonian* const* hs, int n_h, const kg_ru
 }
 
 kg_status kg_batched_tuning(int* block_width, double* ms_per_step, int* n_ctas, int max_log, int* log_width,
-                            double* log_ms) {
-    if (!g_batch || !g_batch->tuned_rb) return fail(KG_EINVAL, "batched: no tuned batch yet");
-    if (block_width) *block_width = g_batch->tuned_rb;
+                            int* log_ctas, double* log_ms) {
+    clear_error();
+    if (!g_batch || !g_batch->tuned_cfg) return fail(KG_EINVAL, "batched: no tuned batch yet");
+    if (block_width) *block_width = g_batch->tuned_cfg / 8;
     if (ms_per_step) *ms_per_step = g_batch->tuned_ms_per_step;
-    if (n_ctas) *n_ctas = g_batch->sched[g_batch->tuned_rb].n_cta;
+    if (n_ctas) *n_ctas = g_batch->sched[g_batch->tuned_cfg].n_cta;
     for (int k = 0; k < max_log && k < (int)g_batch->tuning_log.size(); k++) {
-        if (log_width) log_width[k] = g_batch->tuning_log[k].first;
-        if (log_ms) log_ms[k] = g_batch->tuning_log[k].second;
+        if (log_width) log_width[k] = g_batch->tuning_log[k].rb;
+        if (log_ctas) log_ctas[k] = g_batch->tuning_log[k].n_cta;
+        if (log_ms) log_ms[k] = g_batch->tuning_log[k].ms;
     }
     return KG_OK;
 }

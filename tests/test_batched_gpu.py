@@ -57,7 +57,11 @@ def test_batched_64_vectors_autotuned():
     got = kg.batched_dos_moments(hs, phis, 64)
     t = kg.batched_tuning()
     assert t["block_width"] in (8, 16, 32, 64)
-    assert sorted(bw for bw, _ in t["log"]) == [8, 16, 32, 64]
+    # every block width with both tile schedules (one occupancy wave of CTAs, or half)
+    assert sorted(bw for bw, _, _ in t["log"]) == [8, 8, 16, 16, 32, 32, 64, 64]
+    for bw in (8, 16, 32, 64):
+        ctas = sorted(c for w_, c, _ in t["log"] if w_ == bw)
+        assert ctas[0] < ctas[1] and ctas[0] >= len(ws)
     for i, (h, phi) in enumerate(zip(hs, phis)):
         assert _rel(got[i], kg.dos_moments(h, phi, 64)) < 1e-12
     # repeated calls replay the captured graph and give identical results
