@@ -135,11 +135,35 @@ __global__ void __launch_bounds__(kBThreads) batched_kpm_kernel(BatchArgs a) {
         const double ec = n == 0 ? 1.0 : 2.0;
         Dot64 acc0[kChunks], acc1[kChunks];
         // one thread covers kChunks vectors of a site, so the index loads are amortised over
-        // them; prefetching the next site's indices measured slower here (the extra registers
-        // cost occupancy at the narrow block widths, where a thread holds many vectors)
-        for (int64_t site = s0 + sl; site < s1; site += kSitesPerPass) {
-            const int32_t i0 = __ldg(a.idx + site), i1 = __ldg(a.idx + n_total + site),
-                          i2 = __ldg(a.idx + 2 * n_total + site);
+        // them.  With one vector per thread (block width R) the next site's indices are
+        // loaded one iteration ahead; at narrower widths the extra registers cost occupancy.
+        constexpr bool kPrefetch = kChunks == 1;
+        int64_t site = s0 + sl;
+        int32_t j0 = 0, j1 = 0, j2 = 0;
+        if constexpr (kPrefetch) {
+            if (site < s1) {
+                j0 = __ldg(a.idx + site);
+                j1 = __ldg(a.idx + n_total + site);
+                j2 = __ldg(a.idx + 2 * n_total + site);
+            }
+        }
+        for (; site < s1; site += kSitesPerPass) {
+            int32_t i0, i1, i2;
+            if constexpr (kPrefetch) {
+                i0 = j0;
+                i1 = j1;
+                i2 = j2;
+                const int64_t nxt = site + kSitesPerPass;
+                if (nxt < s1) {
+                    j0 = __ldg(a.idx + nxt);
+                    j1 = __ldg(a.idx + n_total + nxt);
+                    j2 = __ldg(a.idx + 2 * n_total + nxt);
+                }
+            } else {
+                i0 = __ldg(a.idx + site);
+                i1 = __ldg(a.idx + n_total + site);
+                i2 = __ldg(a.idx + 2 * n_total + site);
+            }
             double e = 0.0;
             if constexpr (ONSITE) e = ec * __ldg(a.onsite + site);
 #pragma unroll
