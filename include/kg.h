@@ -246,8 +246,8 @@ kg_status kg_batched_test_stall(int cta);
 
 /* A small network trained on sigma(E, t) curves the method generates, used to predict
  * ensemble-averaged sigma(E, t) across vacancy concentrations (the method itself stays
- * the fallback and the judge of its error).  Architecture: 3 inputs -> 4 hidden layers
- * of 256 GELU units -> 1 output; BF16 weights and activations at the matrix-multiply
+ * the fallback and the reference for its error).  Architecture: 3 inputs -> 4 hidden layers
+ * of 256 GELU units (tanh form) -> 1 output; BF16 weights and activations at the matrix-multiply
  * inputs with FP32 accumulation (the 256 x 256 layers on the tcgen05 tensor cores),
  * FP32 master weights, Adam (beta1 0.9, beta2 0.999, eps 1e-8), loss = mean (y - t)^2.
  * Flat FP32 parameter layout (KG_MLP_PARAMS values): W1 [256][3], b1 [256], then for

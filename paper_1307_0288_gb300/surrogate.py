@@ -6,7 +6,7 @@ sums give the Green-Kubo running conductivity sigma^GK(E, t) (Eqs. 6, 30, 35) on
 energy grid and the correlation times t_m.  A small MLP (kg_mlp, BF16 tensor-core
 kernels) learns (log n, E / E_max, log t) -> sigma.  Concentrations held out of the
 training set are predicted and compared with the ensemble average of plain-method runs
-at those concentrations; the method stays the fallback and the judge of the error.
+at those concentrations; the method stays the fallback and the reference for the error.
 """
 from __future__ import annotations
 
@@ -105,7 +105,7 @@ def generate(grid: Grid, n_conc: int = 40, seeds: int = 5, held_out=None, precis
         held_out = list(range(2, n_conc, 5))
     ds = Dataset(grid, conc, seeds, list(held_out))
     for i, c in enumerate(conc):
-        # held-out concentrations are the judge: plain FP64 runs
+        # held-out concentrations are the reference: plain FP64 runs
         prec = KG_FP64 if i in held_out else (train_precision if train_precision is not None else precision)
         for s in range(seeds):
             sig, sec, emax = sigma_surface(float(c), 7000 + 10 * i + s, grid, prec)

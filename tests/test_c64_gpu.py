@@ -4,7 +4,7 @@ FP64 Bessel/Jackson coefficients, moments and time integration.
 
 Errors are stated against the FP64 oracle for the moments (norm: max |dC| / max |C|
 per vector) and against the FP64 GPU path for sigma(E, t) (max over E and t of
-|d sigma| / max |sigma|), the quantity the precision mode is judged by (<= 1e-5).
+|d sigma| / max |sigma|), the quantity the precision mode is held to (<= 1e-5).
 """
 import numpy as np
 import pytest
