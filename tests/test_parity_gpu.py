@@ -228,6 +228,21 @@ def test_invalid_runs_are_rejected():
         kg.dos_moments(h, w.vectors(1), 0)
 
 
+@pytest.mark.parametrize("precision,tol", [(kg.KG_FP64, TOL_MOMENTS), (kg.KG_C64, 2e-5)])
+def test_vac_and_msd_at_the_maximum_block_of_64_vectors(precision, tol):
+    """R = 64, the largest vector block: the first and last vectors of the block against
+    the oracle (the complex64 path runs its float4 pair kernels at their widest)."""
+    w = ki.sheet_cells(12, 10, vacancy_conc=0.02, lattice_seed=21, n_vec=64)
+    h = kg.from_workload(w)
+    ho = oracle.from_workload(w)
+    phi = w.vectors(64)
+    v = kg.vac(h, phi, 96, 3, 1.0, precision=precision)
+    m = kg.msd(h, phi, 96, 3, 2.0, precision=precision)
+    for r in (0, 63):
+        assert _rel(v[r], oracle.vac_moments(ho, phi[:, r], 96, 3, 1.0)) < tol, r
+        assert _rel(m[r], oracle.msd_moments(ho, phi[:, r], 96, 3, 2.0)) < tol, r
+
+
 def test_fp64_moment_range_and_non_finite_results():
     """The FP64 path forms its inner products in double-float arithmetic: vector entries
     scaled by 2^40 or 2^-40 still give the oracle's moments at 1e-10 (the moments scale
