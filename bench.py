@@ -45,6 +45,7 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "msd-sheet-2048x1024-vac0.5pct-R4-M3000-dt2"
 BATCHED_WORKLOAD = "dos-zgnr16-uneven-anderson-R64-M2000-batched"
 SURROGATE_WORKLOAD = "surrogate-mlp-3x256x4-bf16-batch1M"
+SMALL_WORKLOAD = "vac-sheet-64x64-vac1pct-R1-M512-Nc10-dt1"
 CELLS, VAC, R, M, DT, PREC = WORKLOADS[DEFAULT_WORKLOAD]
 METRIC = "Chebyshev site-updates/s and HBM GB/s vs peak; σ(E,t) time at 1e-5 err vs FP64"
 UNIT = "site-updates/s"
@@ -588,6 +589,93 @@ def run_surrogate(args):
     print(json.dumps(line), flush=True)
 
 
+def run_small(args):
+    """The small VAC case (4096-site sheet, 1 % vacancies, one vector, M = 512, 10
+    correlation times of dt = hbar/gamma0, sigma^GK on 201 energies): one step = one whole
+    run.  Latency-bound: every launch covers only 4096 site-vectors."""
+    import torch
+    import paper_1307_0288_gb300 as kg
+
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    m, nc, dt = 512, 10, 1.0
+    w = ki.sheet_cells(32, 32, vacancy_conc=0.01, n_vec=1)
+    stream = torch.cuda.Stream()
+    h = kg.from_workload(w, stream=stream)
+    n_p = len(kg.bessel_series(h.emax_ev * dt / w.gamma0_ev, TOL))
+    phi_host = torch.from_numpy(w.vectors(1)).pin_memory()
+    phi = phi_host.to("cuda")
+    out = torch.zeros((1, nc, m), dtype=torch.complex128, device="cuda")
+    en = np.linspace(-3 * w.gamma0_ev, 3 * w.gamma0_ev, 201)
+    t_fs = dt * kg.HBAR_EV_FS / w.gamma0_ev
+
+    def one_run(dst):
+        kg.vac(h, phi, m, nc, dt, bessel_tol=TOL, out=dst)
+
+    for _ in range(args.warmup):
+        one_run(out)
+    torch.cuda.synchronize()
+    kg.timing_enable(h, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_run(out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    cnt = kg.timing_read(h)
+    kg.timing_enable(h, False)
+    # sigma^GK(E, t) on the host from the last run's moments (Eqs. 6, 31)
+    t0 = time.perf_counter()
+    dens = kg.kpm_sum(out.cpu().numpy()[0].real, en, h.emax_ev, h.area_nm2)
+    kg.conductivity(kg.KG_SIGMA_GK, dens, t_fs)
+    sums_s = time.perf_counter() - t0
+    # end to end: host input and output through the same call
+    out_host = torch.zeros((1, nc, m), dtype=torch.complex128).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    kg.vac(h, phi_host, m, nc, dt, bessel_tol=TOL, out=out_host)
+    e2e_s = time.perf_counter() - t0
+    # paper-counted work of one run: per time, M - 1 KPM steps; per time step, two chains
+    # of N_p - 1 Chebyshev-Bessel terms (Algorithm 2)
+    work = float(w.n_sites) * (nc * (m - 1) + (nc - 1) * 2 * (n_p - 1))
+    per_run_s = ms * 1e-3 / args.steps
+    peaks = _peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    bytes_run = w.n_sites * (nc * m * (64 + 12) + (nc - 1) * n_p * 2 * 80)
+    achieved = bytes_run / per_run_s / 1e9
+    line = {
+        "metric": METRIC, "value": work / per_run_s, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": SMALL_WORKLOAD, "sites": w.n_sites, "vacancies": len(w.vacancies),
+                   "vectors": 1, "moments": m, "times": nc, "energies": 201, "bessel_terms": n_p,
+                   "us_per_run": per_run_s * 1e6, "host_sums_us": sums_s * 1e6,
+                   "l2": "working set 0.3 MB stays in L2; one step = one whole run"},
+        "roofline": {"bound": "hbm", "kernel": "kpm_gen_kernel<double,1> (VAC KPM step, 4096 site-vectors)",
+                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": None, "peak_source": "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback",
+                     "note": "latency-bound: a launch covers 4096 site-vectors; the fraction says so"},
+        "gpu_launches": int(cnt["kpm_launches"] + cnt["evolve_launches"] + cnt["other_launches"]),
+        "clocks": clk,
+        "e2e": {"value": work / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(phi_host.numel() * 16),
+                "d2h_bytes_per_step": int(out_host.numel() * 16), "seconds": e2e_s},
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        ho = oracle.from_workload(w)
+        t0 = time.perf_counter()
+        oracle.vac_moments(ho, w.vectors(1)[:, 0], m, nc, dt)
+        sec = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": work / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"the whole run (VAC, 10 times, M = 512) in the oracle, one host "
+                                          f"thread: {sec:.2f} s"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -595,12 +683,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCHED_WORKLOAD, SURROGATE_WORKLOAD],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCHED_WORKLOAD, SURROGATE_WORKLOAD, SMALL_WORKLOAD],
                     default=DEFAULT_WORKLOAD)
     args = ap.parse_args()
     global CELLS, VAC, R, M, DT, PREC, CONFIG_NAME
     if args.workload == BATCHED_WORKLOAD:
         return run_batched(args)
+    if args.workload == SMALL_WORKLOAD:
+        return run_small(args)
     if args.workload == SURROGATE_WORKLOAD:
         return run_surrogate(args)
     CELLS, VAC, R, M, DT, PREC = WORKLOADS[args.workload]
