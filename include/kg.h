@@ -61,6 +61,8 @@ int kg_abi_version(void);
 #define KG_SHEET 0  /* 2D graphene, periodic in x and y, transport along x (zigzag)  */
 #define KG_ZGNR 1   /* zigzag ribbon, periodic in x, open in y, transport along x     */
 #define KG_AGNR 2   /* armchair ribbon, periodic in y, open in x, transport along y   */
+#define KG_SHEET_OPEN_X 3  /* sheet open along the transport direction x (periodic in y):
+                            * the non-periodic boundary of Sec. 5.1's length study      */
 
 /* Sample geometry (Sec. 2): nx dimer lines along the zigzag direction, ny zigzag
  * chains; N = nx * ny carbon sites, site (i, j) numbered n = j * nx + i.  Position
@@ -69,7 +71,7 @@ int kg_abi_version(void);
  * on-site energies; the library works with H~ = H / emax_ev, so emax_ev must bound
  * the spectrum (|E| < emax_ev), e.g. 1.05 (3 gamma0 + W/2) for Anderson width W. */
 typedef struct {
-    int32_t kind;       /* KG_SHEET, KG_ZGNR or KG_AGNR */
+    int32_t kind;       /* KG_SHEET, KG_ZGNR, KG_AGNR or KG_SHEET_OPEN_X */
     int32_t reserved;   /* must be 0 */
     int64_t nx;         /* N_x */
     int64_t ny;         /* N_y */

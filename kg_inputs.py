@@ -33,7 +33,7 @@ STREAM_VACANCY = 0
 STREAM_ANDERSON = 1
 STREAM_VECTOR0 = 16  # random vector r uses stream STREAM_VECTOR0 + r
 
-SHEET, ZGNR, AGNR = 0, 1, 2
+SHEET, ZGNR, AGNR, SHEET_OPEN_X = 0, 1, 2, 3
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:

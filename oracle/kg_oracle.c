@@ -41,6 +41,7 @@ int ora_get_mutation(void) { return g_mutation; }
  * kind 0: 2D sheet, periodic in x and y, transport along x.
  * kind 1: zigzag ribbon (ZGNR), periodic in x, open in y, transport along x.
  * kind 2: armchair ribbon (AGNR), periodic in y, open in x, transport along y.
+ * kind 3: sheet open in x (the transport direction), periodic in y, transport along x.
  */
 static void ora_position(int64_t i, int64_t j, double a, double* x, double* y) {
     *x = (double)i * sqrt(3.0) * a / 2.0;
@@ -60,7 +61,7 @@ static double min_image(double d, double len, int periodic) {
 static int ora_bonded_sites(int kind, int64_t nx, int64_t ny, double a,
                             int64_t i, int64_t j, int64_t* nb) {
     const int px = (kind == 0 || kind == 1);
-    const int py = (kind == 0 || kind == 2);
+    const int py = (kind == 0 || kind == 2 || kind == 3);
     const double lx = sqrt(3.0) * (double)nx * a / 2.0, ly = 1.5 * (double)ny * a;
     double x0, y0;
     ora_position(i, j, a, &x0, &y0);
@@ -100,7 +101,7 @@ int64_t ora_build_hamiltonian(int kind, int64_t nx, int64_t ny, double a, double
                               int64_t* row_ptr, int64_t* col, double* val, double* disp,
                               double* diag) {
     const int px = (kind == 0 || kind == 1);
-    const int py = (kind == 0 || kind == 2);
+    const int py = (kind == 0 || kind == 2 || kind == 3);
     const double lx = sqrt(3.0) * (double)nx * a / 2.0, ly = 1.5 * (double)ny * a;
     const int64_t n_sites = nx * ny;
     int64_t nnz = 0;

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-KG_SHEET, KG_ZGNR, KG_AGNR = 0, 1, 2
+KG_SHEET, KG_ZGNR, KG_AGNR, KG_SHEET_OPEN_X = 0, 1, 2, 3
 KG_FP64, KG_C64 = 0, 1
 KG_OP_H, KG_OP_XH, KG_OP_V = 0, 1, 2
 KG_U_FORWARD, KG_U_BACKWARD, KG_U_COMMUTATOR = 0, 1, 2

@@ -27,12 +27,12 @@ void clear_error() { g_last_error.clear(); }
 // ---------------------------------------------------------------------------------
 
 static bool periodic_x(int kind) { return kind == KG_SHEET || kind == KG_ZGNR; }
-static bool periodic_y(int kind) { return kind == KG_SHEET || kind == KG_AGNR; }
+static bool periodic_y(int kind) { return kind == KG_SHEET || kind == KG_AGNR || kind == KG_SHEET_OPEN_X; }
 
 kg_status build_host_lattice(const kg_lattice* lat, const int64_t* vacancies, int64_t n_vac,
                              HostLattice* out) {
     if (!lat) return fail(KG_EINVAL, "lattice is NULL");
-    if (lat->kind < KG_SHEET || lat->kind > KG_AGNR) return fail(KG_EINVAL, "unknown lattice kind");
+    if (lat->kind < KG_SHEET || lat->kind > KG_SHEET_OPEN_X) return fail(KG_EINVAL, "unknown lattice kind");
     if (lat->reserved != 0) return fail(KG_EINVAL, "kg_lattice.reserved must be 0");
     const int kind = lat->kind;
     const int64_t nx = lat->nx, ny = lat->ny;

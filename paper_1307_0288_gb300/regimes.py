@@ -91,24 +91,38 @@ def window_length(curves, e_lo: float, e_hi: float):
 # ------------------------------------------------------------------ ballistic
 
 def run_ballistic(cells=((512, 512), (1024, 512)), n_vec: int = 4, n_moments: int = 2000,
-                  n_times: int = 21, dt: float = 10.0, window=(0.2, 0.5)):
-    """Pristine periodic sheets of two lengths along the zigzag transport direction
-    (1024 x 1024 and 2048 x 1024 sites: 126 nm and 252 nm).  Returns L(t) over the
-    energy window, its ratio to sqrt(2) v_F t, and the difference between the lengths."""
+                  n_times: int = 21, dt: float = 10.0, window=(0.2, 0.5), open_cells=None,
+                  open_times: int = 61, open_dt: float = 41.0):
+    """Pristine sheets along the zigzag transport direction.  Periodic samples (default
+    1024 x 1024 and 2048 x 1024 sites: 126 nm and 252 nm): L(t) over the energy window,
+    its ratio to sqrt(2) v_F t, and the difference between the two lengths.  Samples open
+    along x (open_cells, e.g. (512, 512): 126 nm), the non-periodic boundary of Sec. 5.1, run
+    for open_times steps of open_dt: L(t) grows ballistically and then stays below the sample
+    length (classical free flight between the two ends, with uniformly spread starting points
+    and an isotropic velocity, peaks near 0.93 L_x at t = L_x / v_F and settles at
+    2 L_x / sqrt(6) = 0.82 L_x).  dt in hbar/gamma0 (41 = 10 fs at gamma0 = 2.7 eV)."""
     en = np.linspace(-1.0, 1.0, 201)
     v_f = fermi_velocity()
     out = {"v_f_nm_per_fs": v_f, "window_ev": list(window), "samples": []}
     lengths = []
-    for cx, cy in cells:
-        w = ki.sheet_cells(cx, cy, n_vec=n_vec)
-        c = einstein_curves(w, n_vec, n_moments, n_times, dt, en, block=n_vec)
+    runs = [(ki.SHEET, cx, cy, n_times, dt) for cx, cy in cells]
+    if open_cells is not None:
+        runs.append((ki.SHEET_OPEN_X, open_cells[0], open_cells[1], open_times, open_dt))
+    for kind, cx, cy, nt, step in runs:
+        w = ki.Workload(kind, 2 * cx, 2 * cy, n_vec=n_vec)
+        c = einstein_curves(w, n_vec, n_moments, nt, step, en, block=n_vec)
         length = window_length(c, *window)
         t = c["t_fs"]
         ratio = length[1:] / (np.sqrt(2.0) * v_f * t[1:])
-        lengths.append(length)
-        out["samples"].append({"sites": w.n_sites, "sample_length_nm": w.nx * np.sqrt(3) / 2 * w.bond_nm,
-                               "t_fs": t.tolist(), "L_nm": length.tolist(),
-                               "ratio_to_sqrt2_vF_t": ratio.tolist(), "gpu_seconds": c["gpu_seconds"]})
+        lx = w.nx * np.sqrt(3) / 2 * w.bond_nm
+        entry = {"boundary_x": "periodic" if kind == ki.SHEET else "open", "sites": w.n_sites,
+                 "sample_length_nm": lx, "t_fs": t.tolist(), "L_nm": length.tolist(),
+                 "ratio_to_sqrt2_vF_t": ratio.tolist(), "gpu_seconds": c["gpu_seconds"]}
+        if kind == ki.SHEET:
+            lengths.append(length)
+        else:
+            entry["L_over_sample_length"] = (length / lx).tolist()
+        out["samples"].append(entry)
     if len(lengths) == 2:
         out["max_rel_diff_between_lengths"] = float(np.max(np.abs(lengths[0][1:] - lengths[1][1:])
                                                            / lengths[1][1:]))
@@ -217,7 +231,7 @@ def main(argv=None):
     res = {}
     t0 = time.perf_counter()
     if a.which in ("ballistic", "all"):
-        res["ballistic"] = run_ballistic()
+        res["ballistic"] = run_ballistic(open_cells=(512, 512))
     if a.which in ("diffusive", "all"):
         res["diffusive"] = run_diffusive()
     if a.which in ("localized", "all"):

@@ -43,7 +43,9 @@ def test_neighbor_table_matches_oracle_lattice():
              ki.zgnr(7, 9, vacancy_conc=0.03, lattice_seed=2),
              ki.Workload(ki.AGNR, 9, 12, vacancy_conc=0.04, lattice_seed=3),
              ki.Workload(ki.SHEET, 4, 2),
-             ki.Workload(ki.AGNR, 2, 4)]
+             ki.Workload(ki.AGNR, 2, 4),
+             ki.Workload(ki.SHEET_OPEN_X, 7, 6, vacancy_conc=0.05, lattice_seed=4),
+             ki.Workload(ki.SHEET_OPEN_X, 2, 2)]
     for w in cases:
         idx = kg.lattice_neighbors(w.kind, w.nx, w.ny, w.vacancies)
         h = oracle.from_workload(w)
@@ -55,7 +57,8 @@ def test_neighbor_table_matches_oracle_lattice():
 
 def test_invalid_lattices_are_rejected():
     for kind, nx, ny in [(ki.SHEET, 3, 4), (ki.SHEET, 2, 4), (ki.SHEET, 4, 3), (ki.ZGNR, 5, 3),
-                         (ki.AGNR, 1, 4), (ki.SHEET, 0, 4)]:
+                         (ki.AGNR, 1, 4), (ki.SHEET, 0, 4), (ki.SHEET_OPEN_X, 1, 4), (ki.SHEET_OPEN_X, 6, 3),
+                         (4, 8, 8)]:
         with pytest.raises(kg.KgError) as e:
             kg.lattice_neighbors(kind, nx, ny)
         assert e.value.status == -1

@@ -40,6 +40,7 @@ def _systems():
         ki.sheet_cells(8, 4, vacancy_conc=0.02, lattice_seed=11),
         ki.zgnr(6, 12, anderson_w_ev=2.0, vacancy_conc=0.01, lattice_seed=3),
         ki.Workload(ki.AGNR, 9, 20, vacancy_conc=0.03, anderson_w_ev=0.5, lattice_seed=5),
+        ki.Workload(ki.SHEET_OPEN_X, 10, 16, vacancy_conc=0.02, anderson_w_ev=0.8, lattice_seed=9),
     ]
 
 

@@ -37,6 +37,7 @@ def _systems():
         ki.zgnr(9, 14, anderson_w_ev=1.5, vacancy_conc=0.01, lattice_seed=18),
         ki.Workload(ki.AGNR, 9, 24, vacancy_conc=0.03, lattice_seed=19),
         ki.sheet_cells(25, 13, vacancy_conc=0.01, lattice_seed=20),   # 1300 sites: ragged tail
+        ki.Workload(ki.SHEET_OPEN_X, 14, 12, vacancy_conc=0.02, anderson_w_ev=0.7, lattice_seed=22),
     ]
 
 

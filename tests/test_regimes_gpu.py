@@ -25,6 +25,26 @@ def test_pristine_ballistic_length_grows_as_sqrt2_vf_t():
     assert res["max_rel_diff_between_lengths"] < 0.03
 
 
+def test_open_boundary_length_saturates_below_the_sample_length():
+    """Sec. 5.1, non-periodic boundary along the transport direction (126 nm sample): L(t)
+    first follows the periodic sample, then stays below the sample length L_x (classical
+    free flight between the two ends peaks near 0.93 L_x at t = L_x / v_F and settles at
+    0.82 L_x), while L(t) of the periodic sample of the same size keeps growing."""
+    res = regimes.run_ballistic(cells=((512, 128),), n_vec=4, n_moments=1500, n_times=21, dt=41.0,
+                                open_cells=(512, 128), open_times=61, open_dt=41.0)
+    per, opn = res["samples"]
+    assert opn["boundary_x"] == "open" and per["boundary_x"] == "periodic"
+    lx = opn["sample_length_nm"]
+    t = np.array(opn["t_fs"])
+    l_open = np.array(opn["L_nm"])
+    l_per = np.array(per["L_nm"])
+    assert abs(l_open[1] / l_per[1] - 1.0) < 0.08, (l_open[1], l_per[1])     # t = 10 fs
+    late = t >= 1.5 * lx / res["v_f_nm_per_fs"]
+    assert np.all(l_open < lx), l_open / lx
+    assert np.all(l_open[late] > 0.6 * lx), l_open[late] / lx
+    assert l_per[-1] > 1.2 * lx
+
+
 def test_green_kubo_and_einstein_agree_in_the_diffusive_regime():
     """Sheet with 2 % vacancies: sigma^GK (VAC) and sigma^E1 (MSD) from the same vectors
     agree (Sec. 5.2), and sigma_sc by block average is below sigma_sc by maximum."""
