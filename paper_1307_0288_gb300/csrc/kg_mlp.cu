@@ -95,6 +95,44 @@ __device__ __forceinline__ float gelu(float z) {
     return fmaf(hz, tanh_hw(u), hz);
 }
 
+// Two values at once with the packed FP32 instructions of sm_100 and later (mul/fma
+// .f32x2: one instruction, two IEEE round-to-nearest results): the same operations as
+// gelu() in the same order, so the results are bit-identical, at about half the issue
+// slots.  Returns GELU(z0) in the low and GELU(z1) in the high half.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(uint64_t v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ uint64_t gelu2(uint64_t z) {
+    const uint64_t kc = f2_pack(kGeluK * kGeluC, kGeluK * kGeluC), k = f2_pack(kGeluK, kGeluK);
+    const uint64_t u = f2_mul(z, f2_fma(kc, f2_mul(z, z), k));
+    const uint64_t hz = f2_mul(f2_pack(0.5f, 0.5f), z);
+    const float2 uu = f2_unpack(u);
+    return f2_fma(hz, f2_pack(tanh_hw(uu.x), tanh_hw(uu.y)), hz);
+}
+// BF16 pair (low = first) of GELU(z0), GELU(z1).
+__device__ __forceinline__ uint32_t gelu2_bf16(float z0, float z1) {
+    const float2 g = f2_unpack(gelu2(f2_pack(z0, z1)));
+    const __nv_bfloat162 b2 = __floats2bfloat162_rn(g.x, g.y);
+    return *(const uint32_t*)&b2;
+}
+
 __device__ __forceinline__ float gelu_grad(float z) {
     const float z2 = z * z;
     const float t = tanh_hw(kGeluK * fmaf(kGeluC * z, z2, z));
@@ -313,7 +351,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) umma_gemm_kernel(GemmArgs g) 
 // layout with 128 rows, [32 k-chunks][128 rows][8], so that every store of 8 values of a
 // row is one 16-byte word and a warp's 32 rows are conflict-free.
 
-constexpr int kPThreads = 320;          // warps 0-7 compute, 8 loads, 9 MMA + TMEM
+constexpr int kFCW = 16;                          // compute warps of the fused kernel
+constexpr int kFGroups = kFCW / 4;                // column groups: 4 warps cover the 128 TMEM lanes
+constexpr int kFCols = BN / kFGroups;             // accumulator columns per compute warp
+constexpr int kPThreads = (kFCW + 2) * 32;        // + one load warp + one MMA / TMEM warp
+static_assert(kFCols % 32 == 0 && 32 % kFCW == 0, "compute warp split");
 
 // No-swizzle K-major descriptor (layout type 0) with the given LBO / SBO in bytes.
 __device__ __forceinline__ uint64_t ns_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -361,19 +403,21 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // tiles' BF16 activations (2 x 64 KB, the canonical K-major no-swizzle layout of the
 // tiled format) and a ring of three 32 KB weight blocks (64 K values of one 256 x 256
 // layer); TMEM holds one 128 x 256 FP32 accumulator per tile (all 512 columns).
-//   warps 0-7  layer 1 (3 -> 256, CUDA cores) straight into the tile buffer, then every
-//              epilogue: GELU from TMEM back into the tile buffer as the next layer's
-//              operand, and the next layer's bias stored into the accumulator (tcgen05.st)
-//              for its MMAs to accumulate onto; after layer 4 the fused 256 -> 1 output;
-//   warp 8     streams the weight blocks with cp.async.bulk (from L2 after the first tiles),
-//              in the order the MMAs use them: per layer X's four blocks, then Y's;
-//   warp 9     issues the tcgen05 MMAs and owns the TMEM.
+//   warps 0-15  layer 1 (3 -> 256, CUDA cores) straight into the tile buffer, then every
+//               epilogue: GELU from TMEM back into the tile buffer as the next layer's
+//               operand, and the next layer's bias stored into the accumulator (tcgen05.st)
+//               for its MMAs to accumulate onto; after layer 4 the fused 256 -> 1 output.
+//               Warp w reads TMEM lanes 32 (w % 4) .. + 31 (the rule for tcgen05.ld) and
+//               64 columns; four warps per scheduler hide the TMEM, SFU and shared latencies;
+//   warp 16     streams the weight blocks with cp.async.bulk (from L2 after the first tiles),
+//               in the order the MMAs use them: per layer X's four blocks, then Y's;
+//   warp 17     issues the tcgen05 MMAs and owns the TMEM.
 // Per pair the order is L1(X) L1(Y) | M2(X) M2(Y) M3(X) M3(Y) M4(X) M4(Y), and the epilogue
 // of one tile overlaps the other tile's MMAs.  Every wait is bounded.
 constexpr int kFSlots = 3;
 constexpr int kFWAtom = BN * BK * 2;                     // 32 KB: 8 k-chunks x 256 rows x 16 B
 constexpr int kFTile = BM * H * 2;                       // 64 KB
-constexpr int kFSmem = 2 * kFTile + kFSlots * kFWAtom + 2 * 2 * BM * 4 + 128 + 16 + 128;
+constexpr int kFSmem = 2 * kFTile + kFSlots * kFWAtom + 128 + 16 + 128;
 
 struct FArgs {
     const float* x;                  // [rows][3], rows >= n_valid read as zero
@@ -392,11 +436,10 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
     uint8_t* base_ptr = smem_raw + (base - raw);
     const uint32_t sA = base;                                   // tile t at sA + t * kFTile
     const uint32_t sW = base + 2 * kFTile;                      // slot k at sW + k * kFWAtom
-    float* ypart = (float*)(base_ptr + 2 * kFTile + kFSlots * kFWAtom);   // [2 tiles][2 halves][128]
-    const uint32_t bars = base + 2 * kFTile + kFSlots * kFWAtom + 2 * 2 * BM * 4;
+    const uint32_t bars = base + 2 * kFTile + kFSlots * kFWAtom;
     const uint32_t w_full = bars, w_empty = bars + 8 * kFSlots, a_ready = bars + 16 * kFSlots,
                    acc_full = bars + 16 * kFSlots + 16;
-    uint32_t* tmem_slot = (uint32_t*)(base_ptr + 2 * kFTile + kFSlots * kFWAtom + 2 * 2 * BM * 4 + 128);
+    uint32_t* tmem_slot = (uint32_t*)(base_ptr + 2 * kFTile + kFSlots * kFWAtom + 128);
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n_pairs = (p.n_tiles + 1) / 2;
@@ -408,12 +451,12 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
             mbar_init(w_empty + 8 * k, 1);
         }
         for (int t = 0; t < 2; t++) {
-            mbar_init(a_ready + 8 * t, 8);
+            mbar_init(a_ready + 8 * t, kFCW);
             mbar_init(acc_full + 8 * t, 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 9) {
+    if (warp == kFCW + 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(2 * BN)
                      : "memory");
@@ -428,7 +471,7 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
         s_abort = 1;
     };
 
-    if (warp == 8 && lane == 0) {
+    if (warp == kFCW && lane == 0) {
         // weight blocks in MMA order: per pair, per layer, per tile, four K blocks
         int64_t g = 0;
         for (int64_t pr = blockIdx.x; pr < n_pairs && !s_abort; pr += gridDim.x) {
@@ -450,7 +493,7 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
         volatile int never = 0;
         for (int64_t q = (g > kFSlots ? g - kFSlots : 0); q < g; q++)
             if (!pwait(w_full + 8 * (int)(q % kFSlots), (uint32_t)((q / kFSlots) & 1), &never)) atomicExch(p.error, 1);
-    } else if (warp == 9 && lane == 0) {
+    } else if (warp == kFCW + 1 && lane == 0) {
         int64_t g = 0, job[2] = {0, 0};
         uint32_t last_bar = 0, last_parity = 0;
         for (int64_t pr = blockIdx.x; pr < n_pairs && !s_abort; pr += gridDim.x) {
@@ -502,9 +545,9 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
         // every MMA issued must be complete before the TMEM is freed (bounded)
         volatile int never = 0;
         if (last_bar && !pwait(last_bar, last_parity, &never)) atomicExch(p.error, 1);
-    } else if (warp < 8) {
-        // warp w: TMEM lanes (tile rows) 32 (w % 4) .. + 31, accumulator columns of half w / 4
-        const int quarter = warp & 3, half = warp >> 2;
+    } else if (warp < kFCW) {
+        // warp w: TMEM lanes (tile rows) 32 (w % 4) .. + 31, accumulator columns of group w / 4
+        const int quarter = warp & 3, grp = warp >> 2;
         const int rl = quarter * 32 + lane;
         const float* W1 = p.params + kOffW1;
         const float* b1 = p.params + kOffB1;
@@ -516,8 +559,8 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
         auto preload_bias = [&](int t, int layer) {
             const float4* bias4 = (const float4*)(p.params + layer_b(layer));
 #pragma unroll 1
-            for (int cb = 0; cb < 4; cb++) {
-                const int col0 = half * 128 + cb * 32;
+            for (int cb = 0; cb < kFCols / 32; cb++) {
+                const int col0 = grp * kFCols + cb * 32;
                 uint32_t v[32];
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
@@ -531,7 +574,7 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         };
-        // all eight warps have written the tile's operand and the accumulator's bias: publish
+        // all compute warps have written the tile's operand and the accumulator's bias: publish
         auto publish = [&](int t) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -539,7 +582,7 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
             if (lane == 0) mbar_arrive(a_ready + 8 * t);
         };
         for (int64_t pr = blockIdx.x; pr < n_pairs; pr += gridDim.x) {
-            // layer 1: warp w covers k-chunks 4w .. 4w + 3 (32 columns), lane covers rows
+            // layer 1: warp w covers k-chunks 2w, 2w + 1 (16 columns), lane covers rows
             // lane + 32 i; the column weights are warp-uniform 16-byte loads
             for (int t = 0; t < 2; t++) {
                 const int64_t row0 = (2 * pr + t) * BM;
@@ -555,8 +598,8 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                     }
                 }
 #pragma unroll 1
-                for (int cq = 0; cq < 4; cq++) {
-                    const int ch = warp * 4 + cq;                  // k-chunk: columns 8 ch .. 8 ch + 7
+                for (int cq = 0; cq < 32 / kFCW; cq++) {
+                    const int ch = warp * (32 / kFCW) + cq;        // k-chunk: columns 8 ch .. 8 ch + 7
                     float w[24], bb[8];
                     const float4* w4 = (const float4*)(W1 + ch * 24);
 #pragma unroll
@@ -575,10 +618,13 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                         uint32_t packed[4];
 #pragma unroll
                         for (int e = 0; e < 8; e += 2) {
-                            const float v0 = fmaf(w[3 * e], xr[i][0], fmaf(w[3 * e + 1], xr[i][1], fmaf(w[3 * e + 2], xr[i][2], bb[e])));
-                            const float v1 = fmaf(w[3 * e + 3], xr[i][0], fmaf(w[3 * e + 4], xr[i][1],
-                                                  fmaf(w[3 * e + 5], xr[i][2], bb[e + 1])));
-                            const __nv_bfloat162 b2 = __floats2bfloat162_rn(gelu(v0), gelu(v1));
+                            // columns e, e + 1 side by side: z = W1 x + b1 with packed FMAs
+                            uint64_t z = f2_pack(bb[e], bb[e + 1]);
+                            z = f2_fma(f2_pack(w[3 * e + 2], w[3 * e + 5]), f2_pack(xr[i][2], xr[i][2]), z);
+                            z = f2_fma(f2_pack(w[3 * e + 1], w[3 * e + 4]), f2_pack(xr[i][1], xr[i][1]), z);
+                            z = f2_fma(f2_pack(w[3 * e], w[3 * e + 3]), f2_pack(xr[i][0], xr[i][0]), z);
+                            const float2 g = f2_unpack(gelu2(z));
+                            const __nv_bfloat162 b2 = __floats2bfloat162_rn(g.x, g.y);
                             packed[e >> 1] = *(const uint32_t*)&b2;
                         }
                         st_shared_v4(sA + t * kFTile + (uint32_t)((ch * BM + lane + 32 * i) * 16),
@@ -588,7 +634,7 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                 preload_bias(t, 2);
                 publish(t);
             }
-            // layers 2-4: epilogues.  After an abort every wait returns at once, but all eight
+            // layers 2-4: epilogues.  After an abort every wait returns at once, but all compute
             // warps still run every iteration, so each reaches every named barrier below.
             for (int l = 0; l < 3; l++)
                 for (int t = 0; t < 2; t++) {
@@ -596,14 +642,17 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                     job[t]++;
                     if (!ok) {
                         give_up();
-                        if (l == 2) asm volatile("bar.sync 1, 256;" ::: "memory");
+                        if (l == 2) {
+                            asm volatile("bar.sync 1, %0;" ::"n"(kFCW * 32) : "memory");
+                            asm volatile("bar.sync 1, %0;" ::"n"(kFCW * 32) : "memory");
+                        }
                         continue;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     float ysum = 0.0f;
 #pragma unroll 1
-                    for (int cb = 0; cb < 4; cb++) {
-                        const int col0 = half * 128 + cb * 32;
+                    for (int cb = 0; cb < kFCols / 32; cb++) {
+                        const int col0 = grp * kFCols + cb * 32;
                         uint32_t v[32];
                         KG_TMEM_LD32(tmem + t * BN + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0, v);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -613,21 +662,21 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
 #pragma unroll
                             for (int q = 0; q < 8; q++) {
                                 const float4 f = __ldg(w54 + q);
-                                ysum = fmaf(gelu(__uint_as_float(v[4 * q])), f.x, ysum);
-                                ysum = fmaf(gelu(__uint_as_float(v[4 * q + 1])), f.y, ysum);
-                                ysum = fmaf(gelu(__uint_as_float(v[4 * q + 2])), f.z, ysum);
-                                ysum = fmaf(gelu(__uint_as_float(v[4 * q + 3])), f.w, ysum);
+                                const float2 g0 = f2_unpack(gelu2(f2_pack(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]))));
+                                const float2 g1 =
+                                    f2_unpack(gelu2(f2_pack(__uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]))));
+                                ysum = fmaf(g0.x, f.x, ysum);
+                                ysum = fmaf(g0.y, f.y, ysum);
+                                ysum = fmaf(g1.x, f.z, ysum);
+                                ysum = fmaf(g1.y, f.w, ysum);
                             }
                         } else {
 #pragma unroll
                             for (int c8 = 0; c8 < 4; c8++) {
                                 uint32_t packed[4];
 #pragma unroll
-                                for (int e = 0; e < 8; e += 2) {
-                                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(
-                                        gelu(__uint_as_float(v[c8 * 8 + e])), gelu(__uint_as_float(v[c8 * 8 + e + 1])));
-                                    packed[e >> 1] = *(const uint32_t*)&b2;
-                                }
+                                for (int e = 0; e < 8; e += 2)
+                                    packed[e >> 1] = gelu2_bf16(__uint_as_float(v[c8 * 8 + e]), __uint_as_float(v[c8 * 8 + e + 1]));
                                 const int chunk = (col0 >> 3) + c8;
                                 st_shared_v4(sA + t * kFTile + (uint32_t)((chunk * BM + rl) * 16),
                                              make_uint4(packed[0], packed[1], packed[2], packed[3]));
@@ -638,20 +687,29 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                         preload_bias(t, l + 3);
                         publish(t);
                     } else {
-                        // accumulator read: the next pair's layer 1 may now be followed by MMAs
+                        // accumulator read: the next pair's layer 1 may now be followed by MMAs.
+                        // The column groups' partial sums meet in the tile's operand buffer,
+                        // which the completed layer-4 MMAs no longer read; the second barrier
+                        // keeps the next pair's layer 1 from overwriting them before they are read.
                         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                        ypart[(t * 2 + half) * BM + rl] = ysum;
-                        asm volatile("bar.sync 1, 256;" ::: "memory");
+                        float* ypart = (float*)(base_ptr + t * kFTile);   // [kFGroups][128]
+                        ypart[grp * BM + rl] = ysum;
+                        asm volatile("bar.sync 1, %0;" ::"n"(kFCW * 32) : "memory");
                         const int64_t grow = (2 * pr + t) * BM + rl;
-                        if (half == 0 && grow < p.n_valid)
-                            p.y[grow] = ypart[(t * 2) * BM + rl] + ypart[(t * 2 + 1) * BM + rl] + b5;
+                        if (grp == 0 && grow < p.n_valid) {
+                            float yv = b5;
+#pragma unroll
+                            for (int q = 0; q < kFGroups; q++) yv += ypart[q * BM + rl];
+                            p.y[grow] = yv;
+                        }
+                        asm volatile("bar.sync 1, %0;" ::"n"(kFCW * 32) : "memory");
                     }
                 }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 9) {
+    if (warp == kFCW + 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
     }
 }
