@@ -9,6 +9,7 @@ import os
 
 import numpy as np
 import pytest
+from scipy import special
 from scipy.special import jv
 
 import kg_inputs as ki
@@ -403,6 +404,42 @@ def test_dos_sum_reproduces_dirac_slope():
     rho = post.kpm_density(mu, en, emax, area)
     exact = 2 * en / (np.pi * (1.5 * G0 * A_NM) ** 2)
     assert np.allclose(rho, exact, rtol=0.02)
+
+
+def _graphene_dos_per_cell(x):
+    """Closed-form DOS of the nearest-neighbour honeycomb per unit cell, spin included, in
+    units of 1/gamma0 at x = E/gamma0 (Hobson and Nierenberg 1953; Castro Neto et al. 2009,
+    the paper's graphene reference): a complete elliptic integral of the first kind."""
+    x = np.abs(x)
+    a = (1 + x) ** 2 - (x * x - 1) ** 2 / 4
+    z0 = np.where(x <= 1, a, 4 * x)
+    z1 = np.where(x <= 1, 4 * x, a)
+    return 4 / np.pi ** 2 * x / np.sqrt(z0) * special.ellipk(np.minimum(z1 / z0, 1 - 1e-16))
+
+
+def test_dos_matches_closed_form_over_the_band():
+    """Eq. (29) with Jackson damping, applied to the exact Bloch-band moments of a
+    512 x 512-site pristine sheet, reproduces the closed-form graphene DOS over the whole
+    band (away from the Dirac point, the van Hove singularity at gamma0 and the band edge
+    at 3 gamma0, where the M = 500 kernel broadening matters) and puts the van Hove peak at
+    E = gamma0.  The closed form itself is checked first: 4 states per cell (2 atoms x 2
+    spins) and the Dirac slope 4 |x| / (sqrt(3) pi)."""
+    n = 2_000_000
+    x = (np.arange(n) + 0.5) * 3.0 / n
+    assert abs(2 * np.sum(_graphene_dos_per_cell(x)) * 3.0 / n - 4.0) < 1e-4
+    assert abs(_graphene_dos_per_cell(np.array([1e-6]))[0] / 1e-6 - 4 / (np.sqrt(3) * np.pi)) < 1e-5
+    nx = ny = 512
+    emax = 1.05 * 3 * G0
+    mu = _chebyshev_trace(_bloch_levels(nx, ny, emax), 500)
+    area = (np.sqrt(3) * nx * A_NM / 2) * (1.5 * ny * A_NM)
+    cell = 3 * np.sqrt(3) / 2 * A_NM ** 2
+    en = np.concatenate([np.linspace(0.2, 2.2, 21), np.linspace(3.3, 7.5, 22), -np.linspace(0.4, 7.4, 8)])
+    rho = post.kpm_density(mu, en, emax, area)
+    exact = _graphene_dos_per_cell(en / G0) / G0 / cell
+    assert np.max(np.abs(rho / exact - 1)) < 0.01, np.abs(rho / exact - 1)
+    e_vh = np.linspace(2.0, 3.4, 1401)
+    peak = e_vh[np.argmax(post.kpm_density(mu, e_vh, emax, area))]
+    assert abs(peak - G0) < 0.02, peak
 
 
 def test_random_vector_trace_is_unbiased():
