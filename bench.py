@@ -655,7 +655,8 @@ def run_small(args):
                    "vectors": 1, "moments": m, "times": nc, "energies": 201, "bessel_terms": n_p,
                    "us_per_run": per_run_s * 1e6, "host_sums_us": sums_s * 1e6,
                    "l2": "working set 0.3 MB stays in L2; one step = one whole run"},
-        "roofline": {"bound": "hbm", "kernel": "kpm_gen_kernel<double,1> (VAC KPM step, 4096 site-vectors)",
+        "roofline": {"bound": "hbm", "kernel": "kpm_cluster_kernel<double,1> (VAC KPM steps, 256 per "
+                                                          "cluster launch, 4096 site-vectors)",
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                      "traffic": None, "peak_source": "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback",
                      "note": "latency-bound: a launch covers 4096 site-vectors; the fraction says so"},

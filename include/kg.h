@@ -237,6 +237,16 @@ kg_status kg_batched_release(void);
  * allocation failures on the host; the handle stays usable once the cap is lifted. */
 kg_status kg_test_alloc_cap(uint64_t bytes);
 
+/* Execution option for small instances (Algorithm 5's recursion loop; no new arithmetic).
+ * When one recursion step of a moment loop needs at most 16 CTAs (FP64: up to 8192
+ * site-vectors; complex64: one vector, up to 4096 sites), a launch per step costs more
+ * than the step, so by default (enable = 1) every 256 steps run in one launch of a single
+ * thread-block cluster whose CTAs separate the steps with the cluster's hardware barrier.
+ * The moments are bitwise those of one launch per step (same grid, same operations, same
+ * reduction order); enable = 0 selects one launch per step for every size.  Process-wide;
+ * takes effect on the next call. */
+kg_status kg_set_small_persistent(int enable);
+
 /* Test hook for failure detection: CTA `cta` of the cached batch stops publishing its
  * step flags after step 0, so its neighbours' bounded waits run out and the next
  * kg_batched_dos_moments returns KG_ETIMEOUT.  -1 turns the hook off. */

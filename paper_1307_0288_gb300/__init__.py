@@ -84,6 +84,7 @@ ABI = [
     ("kg_msd_resume", _I, [_P, ctypes.POINTER(_Run), _P, _P, _P, _P, _P]),
     ("kg_vac_resume", _I, [_P, ctypes.POINTER(_Run), _P, _P, _P, _P, _P]),
     ("kg_test_alloc_cap", _I, [ctypes.c_uint64]),
+    ("kg_set_small_persistent", _I, [_I]),
     ("kg_ftm_dos_moments", _I, [_P, ctypes.POINTER(_Run), _P, _P]),
     ("kg_ftm_sum", _I, [_P, _I, _I, _P, _I, _D, _D, _P]),
     ("kg_ballistic", _I, [_P, _P, _I, _I, _D, _D, _P, _P]),
@@ -321,6 +322,12 @@ def vac_resume(h: Hamiltonian, a, b, n_moments: int, n_times: int, dt: float, *,
 def test_alloc_cap(n_bytes: int):
     """kg_test_alloc_cap: workspace allocations above n_bytes fail with KG_ENOMEM (0 = off)."""
     _check(lib().kg_test_alloc_cap(int(n_bytes)))
+
+
+def set_small_persistent(enable: bool):
+    """kg_set_small_persistent: small instances run each 256 recursion steps in one
+    cluster launch (True, the default) or one launch per step (False)."""
+    _check(lib().kg_set_small_persistent(1 if enable else 0))
 
 
 def ftm_dos_moments(h: Hamiltonian, phi, n_m: int, *, bessel_tol=1e-15, out=None):

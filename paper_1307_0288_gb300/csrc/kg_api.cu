@@ -2,6 +2,7 @@
 // time-evolution drivers (Algorithms 2, 3, 5, 6, 7 of the paper).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include <cmath>
@@ -17,6 +18,10 @@ namespace kg {
 // Test hook: workspace allocations above this many bytes fail as if the device were out
 // of memory (0 = no cap).  Injects KG_ENOMEM on the host, without a real allocation failure.
 static std::atomic<unsigned long long> g_alloc_cap{0};
+
+// Small instances run their moment recursion as one cluster launch per ring of steps
+// (kg_set_small_persistent); 0 = one launch per step everywhere.
+static std::atomic<int> g_small_persistent{1};
 
 // Device buffer owned by the handle.
 struct DevBuf {
@@ -215,6 +220,25 @@ static kg_status kpm_moments(kg_hamiltonian* h, int R, int M, bool sym, const ve
     const V2* cur = b1;
     const V2* prev = phi_r;
     V2* out = b0;
+    if (steps > 0 && g_small_persistent.load() && kpm_cluster_ok<T>(h->dev, R, sym, grid)) {
+        // small instance: each ring's worth of steps in one cluster launch (same moments, bitwise)
+        for (int n0 = 1; n0 <= steps; n0 += kRing) {
+            const int cnt = std::min(kRing, steps - n0 + 1);
+            KG_CUDA_TRY(launch_kpm_cluster<T>(h->dev, R, sym, phi_l, cur, prev, out, ring, (n0 - 1) % kRing, kRing,
+                                              cnt, grid, s));
+            KG_CUDA_TRY(launch_reduce_ring(ring, (n0 - 1) % kRing, cnt, kRing, grid, R, sym, n0, mu, r_stride, M, s));
+            h->counters.kpm_launches += 1;
+            h->counters.other_launches += 1;
+            h->counters.kpm_site_steps += (double)h->n * R * cnt;
+            for (int k = 0; k < cnt; k++) {   // the kernel's pointer rotation, replayed on the host
+                const V2* new_cur = out;
+                prev = cur;
+                out = const_cast<V2*>(cur);
+                cur = new_cur;
+            }
+        }
+        return KG_OK;
+    }
     int pending = 0, first_pending = 1;
     for (int n = 1; n <= steps; n++) {
         double* slab = ring + (int64_t)((n - 1) % kRing) * grid * R * 2;
@@ -726,6 +750,12 @@ kg_status kg_msd_resume(kg_hamiltonian* h, const kg_run* run, const double* psi,
 kg_status kg_test_alloc_cap(uint64_t bytes) {
     clear_error();
     g_alloc_cap.store(bytes);
+    return KG_OK;
+}
+
+kg_status kg_set_small_persistent(int enable) {
+    clear_error();
+    g_small_persistent.store(enable ? 1 : 0);
     return KG_OK;
 }
 

@@ -110,6 +110,21 @@ cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const vec2_t<T>* L,
 template <typename T>
 int kpm_grid(const DevH& H, int R, bool sym);
 
+// Small instances: true when `grid` (the grid of the per-step kernels, at most 16 CTAs)
+// can run as one resident thread-block cluster for this H, R and mode (cached per device).
+template <typename T>
+bool kpm_cluster_ok(const DevH& H, int R, bool sym, int grid);
+
+// The non-first KPM steps n0 .. n0 + nsteps - 1 in one cluster launch of `grid` CTAs:
+// the same arithmetic and partial sums as nsteps per-step launches (bitwise), step k's
+// partials in ring slab (slab0 + k) % ring_size.  cur / prev / out are the blocks of the
+// first of these steps; the kernel rotates them like the per-step loop.
+template <typename T>
+cudaError_t launch_kpm_cluster(const DevH& H, int R, bool sym, const vec2_t<T>* L,
+                               const vec2_t<T>* cur, const vec2_t<T>* prev, vec2_t<T>* out,
+                               double* ring, int slab0, int ring_size, int nsteps, int grid,
+                               cudaStream_t s);
+
 // Reduce per-block partials of a KPM run into moments mu[r * r_stride + n].
 //   first: partial [grid][R][A] of the first step (A = 2 sym, 4 gen)
 //   ring:  partial slabs [ring][grid][R][2]; slab (slab0 + b) % ring belongs to step n0 + b

@@ -242,6 +242,79 @@ __global__ void __launch_bounds__(kBlock<T>) kpm_gen_kernel(DevH H, const vec2_t
 }
 
 // --------------------------------------------------------------------------------
+// Small instances: many KPM steps in one launch of one thread-block cluster.
+// A 4096-site sheet with one vector is 8 CTAs of work per step, and one launch per step
+// then costs more than the step.  Here the grid (the same grid the per-step kernels use,
+// at most 16 CTAs) is a single cluster that runs the recursion steps n0 .. n0+nsteps-1:
+// each step does exactly what kpm_sym_kernel / kpm_gen_kernel (not FIRST) does with that
+// grid -- the same items per thread, the same operations in the same order, the same
+// block reduction into ring slab (slab0 + k) % ring_size -- so the moments are bitwise
+// those of the per-step launches.  Steps are separated by the cluster's hardware barrier
+// (arrive.release / wait.acquire at cluster scope), which every thread of every CTA
+// reaches once per step: there is no spin loop.  Vectors written within the launch are
+// read with L2-only loads (ld.global.cg); the rotation of the three block pointers is
+// the host's (out <- cur's block after the step, in place over phi_{n-1}).
+// --------------------------------------------------------------------------------
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+template <typename T, int R, bool ONSITE, bool SYM>
+__global__ void __launch_bounds__(kBlock<T>) kpm_cluster_kernel(DevH H, const vec2_t<T>* __restrict__ L,
+                                                               const vec2_t<T>* cur, const vec2_t<T>* prev,
+                                                               vec2_t<T>* out, double* __restrict__ ring,
+                                                               int slab0, int ring_size, int nsteps) {
+    using V2 = vec2_t<T>;
+    constexpr int NT = kBlock<T>;
+    const int64_t n_items = H.n * R;
+    const int64_t stride = (int64_t)gridDim.x * NT;
+    const int r = threadIdx.x & (R - 1);
+    const T c = (T)(2.0 * H.h);
+    for (int k = 0; k < nsteps; k++) {
+        Acc<T> a0, a1;
+        int64_t w = (int64_t)blockIdx.x * NT + threadIdx.x;
+        Idx3 nid;
+        if (w < n_items) nid = load_idx(H.idx, H.istride, w / R);
+        for (; w < n_items; w += stride) {
+            const int64_t n = w / R;
+            Nbr<T> g;
+            g.a = __ldcg(cur + (int64_t)nid.i0 * R + r);
+            g.b = __ldcg(cur + (int64_t)nid.i1 * R + r);
+            g.c = __ldcg(cur + (int64_t)nid.i2 * R + r);
+            g.x = __ldcg(cur + n * R + r);
+            T e = 0;
+            if constexpr (ONSITE) e = (T)(2.0 * __ldg(H.onsite + n));
+            const V2 z = __ldcg(prev + w);
+            V2 l = mk<T>(0, 0);
+            if constexpr (!SYM) l = __ldg(L + w);
+            if (w + stride < n_items) nid = load_idx(H.idx, H.istride, (w + stride) / R);
+            const T yr = hop<T>(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
+            const T yi = hop<T>(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
+            out[w] = mk<T>(yr, yi);
+            if constexpr (SYM) {
+                a0.add_prod(g.x.x, g.x.x);
+                a0.add_prod(g.x.y, g.x.y);
+                a1.add_prod(yr, g.x.x);
+                a1.add_prod(yi, g.x.y);
+            } else {
+                a0.add_prod(l.x, yr);
+                a0.add_prod(l.y, yi);
+                a1.add_prod(l.x, yi);
+                a1.add_prod(-l.y, yr);
+            }
+        }
+        double acc[2] = {a0.value(), a1.value()};
+        double* slab = ring + (int64_t)((slab0 + k) % ring_size) * gridDim.x * R * 2;
+        block_reduce<R, 2, NT>(acc, slab + (int64_t)blockIdx.x * R * 2);
+        cluster_barrier();
+        const V2* next = out;
+        prev = cur;
+        out = const_cast<V2*>(cur);
+        cur = next;
+    }
+}
+
+// --------------------------------------------------------------------------------
 // complex64 KPM steps with 128-bit accesses: for R >= 2 one thread owns the two adjacent
 // vectors (2 r2, 2 r2 + 1) of a site and moves them as one float4, halving the load and
 // store instructions per byte of the HBM-bound FP32 step.  Per-vector partial sums are
@@ -717,6 +790,79 @@ cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const vec2_t<T>* L,
     return cudaGetLastError();
 }
 
+// One launch of `kernel` as a single cluster of `grid` CTAs (grid <= kMaxCluster; above
+// the portable 8 the kernel is allowed the non-portable size).  query = only check that
+// such a cluster can be resident (cudaErrorNotSupported when not).
+constexpr int kMaxCluster = 16;
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_single_cluster(void (*kernel)(KArgs...), int grid, int threads, bool query,
+                                         cudaStream_t s, Args... args) {
+    if (grid < 1 || grid > kMaxCluster) return cudaErrorNotSupported;
+    if (grid > 8) {
+        const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)grid;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (query) {
+        int clusters = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg);
+        if (e != cudaSuccess) return e;
+        return clusters >= 1 ? cudaSuccess : cudaErrorNotSupported;
+    }
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <typename T>
+static cudaError_t kpm_cluster_dispatch(const DevH& H, int R, bool sym, bool query, const vec2_t<T>* L,
+                                        const vec2_t<T>* cur, const vec2_t<T>* prev, vec2_t<T>* out,
+                                        double* ring, int slab0, int ring_size, int nsteps, int grid,
+                                        cudaStream_t s) {
+    if (kPaired<T> && R >= 2) return cudaErrorNotSupported;   // complex64 blocks use the paired kernels
+    const bool ons = H.onsite != nullptr;
+    cudaError_t e = cudaErrorNotSupported;
+    KG_DISPATCH_R(R, if constexpr (!kPaired<T> || RR == 1) { KG_BOOL(ons, ON, KG_BOOL(sym, SY,
+        e = launch_single_cluster(kpm_cluster_kernel<T, RR, ON, SY>, grid, kBlock<T>, query, s, H, L, cur,
+                                  prev, out, ring, slab0, ring_size, nsteps))) });
+    return e;
+}
+
+template <typename T>
+bool kpm_cluster_ok(const DevH& H, int R, bool sym, int grid) {
+    if (grid < 1 || grid > kMaxCluster || (kPaired<T> && R >= 2)) return false;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t key = ((uint64_t)dev << 40) | ((uint64_t)sizeof(T) << 32) | ((uint64_t)R << 16) |
+                         ((uint64_t)grid << 2) | ((uint64_t)(H.onsite != nullptr) << 1) | (uint64_t)sym;
+    static thread_local std::unordered_map<uint64_t, bool> cache;
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    const cudaError_t e = kpm_cluster_dispatch<T>(H, R, sym, true, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                  0, 1, 0, grid, nullptr);
+    if (e != cudaSuccess) cudaGetLastError();   // a refused query must not leak into later launch checks
+    cache[key] = e == cudaSuccess;
+    return e == cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_kpm_cluster(const DevH& H, int R, bool sym, const vec2_t<T>* L, const vec2_t<T>* cur,
+                               const vec2_t<T>* prev, vec2_t<T>* out, double* ring, int slab0, int ring_size,
+                               int nsteps, int grid, cudaStream_t s) {
+    if (nsteps <= 0) return cudaSuccess;
+    return kpm_cluster_dispatch<T>(H, R, sym, false, L, cur, prev, out, ring, slab0, ring_size, nsteps, grid, s);
+}
+
 template <typename T>
 int kpm_grid(const DevH& H, int R, bool sym) {
     const bool ons = H.onsite != nullptr;
@@ -852,6 +998,10 @@ cudaError_t launch_to_c64(const double2* in, float2* out, int64_t n_items, cudaS
                                            const vec2_t<T>*, const vec2_t<T>*, vec2_t<T>*, double*,   \
                                            int, cudaStream_t);                                      \
     template int kpm_grid<T>(const DevH&, int, bool);                                              \
+    template bool kpm_cluster_ok<T>(const DevH&, int, bool, int);                                  \
+    template cudaError_t launch_kpm_cluster<T>(const DevH&, int, bool, const vec2_t<T>*,           \
+                                               const vec2_t<T>*, const vec2_t<T>*, vec2_t<T>*,     \
+                                               double*, int, int, int, int, cudaStream_t);          \
     template cudaError_t launch_evolve<T>(const DevH&, int, int, bool, bool, double, double, double, \
                                           const ChainsT<T>&, cudaStream_t);                        \
     template cudaError_t launch_apply<T>(const DevH&, int, int, double, const vec2_t<T>*,           \
