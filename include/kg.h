@@ -238,13 +238,14 @@ kg_status kg_batched_release(void);
 kg_status kg_test_alloc_cap(uint64_t bytes);
 
 /* Execution option for small instances (Algorithm 5's recursion loop; no new arithmetic).
- * When one recursion step of a moment loop needs at most 16 CTAs (FP64: up to 8192
- * site-vectors; complex64: one vector, up to 4096 sites), a launch per step costs more
- * than the step, so by default (enable = 1) every 256 steps run in one launch of a single
- * thread-block cluster whose CTAs separate the steps with the cluster's hardware barrier.
- * The moments are bitwise those of one launch per step (same grid, same operations, same
- * reduction order); enable = 0 selects one launch per step for every size.  Process-wide;
- * takes effect on the next call. */
+ * When one recursion step of a moment loop needs at most 16 CTAs (up to 8192 site-vectors,
+ * R <= 16), a launch per step costs more than the step, so by default (enable = 1) up to
+ * 256 steps run in one launch of a single thread-block cluster that keeps the vectors in
+ * its shared memory and separates the steps with the cluster's hardware barrier.  The
+ * Chebyshev vectors are bitwise those of one launch per step; the moments' inner
+ * products are summed in another order (double-float sums, agreement to about 1e-15 of
+ * the largest moment).  enable = 0 selects one launch per step for every size.
+ * Process-wide; takes effect on the next call. */
 kg_status kg_set_small_persistent(int enable);
 
 /* Test hook for failure detection: CTA `cta` of the cached batch stops publishing its

@@ -204,7 +204,10 @@ static kg_status kpm_moments(kg_hamiltonian* h, int R, int M, bool sym, const ve
     using V2 = vec2_t<T>;
     PhaseTimer t(h, 0);
     const int grid = kpm_grid<T>(h->dev, R, sym);
-    KG_TRY(ensure_partials(h, R, grid));
+    const int steps = sym ? (M - 1) / 2 : M - 2;   // recursion steps after the first
+    ClusterPlan plan;
+    const bool cluster = steps > 0 && g_small_persistent.load() && kpm_cluster_plan<T>(h->dev, R, sym, &plan);
+    KG_TRY(ensure_partials(h, R, cluster ? std::max(grid, plan.grid) : grid));
     double* pf = (double*)h->part_first.p;
     double* ring = (double*)h->part_ring.p;
     cudaStream_t s = h->stream;
@@ -216,17 +219,16 @@ static kg_status kpm_moments(kg_hamiltonian* h, int R, int M, bool sym, const ve
     h->counters.other_launches += 1;
     h->counters.kpm_site_steps += (double)h->n * R;
     // remaining steps n = 1..S: phi_{n+1} = 2H~phi_n - phi_{n-1}
-    const int steps = sym ? (M - 1) / 2 : M - 2;
     const V2* cur = b1;
     const V2* prev = phi_r;
     V2* out = b0;
-    if (steps > 0 && g_small_persistent.load() && kpm_cluster_ok<T>(h->dev, R, sym, grid)) {
-        // small instance: each ring's worth of steps in one cluster launch (same moments, bitwise)
-        for (int n0 = 1; n0 <= steps; n0 += kRing) {
-            const int cnt = std::min(kRing, steps - n0 + 1);
-            KG_CUDA_TRY(launch_kpm_cluster<T>(h->dev, R, sym, phi_l, cur, prev, out, ring, (n0 - 1) % kRing, kRing,
-                                              cnt, grid, s));
-            KG_CUDA_TRY(launch_reduce_ring(ring, (n0 - 1) % kRing, cnt, kRing, grid, R, sym, n0, mu, r_stride, M, s));
+    if (cluster) {
+        // small instance: each chunk of steps in one cluster launch, vectors in shared memory
+        static_assert(kClusterMaxChunk <= kRing, "a chunk's partial slabs must fit the ring");
+        for (int n0 = 1; n0 <= steps; n0 += plan.chunk) {
+            const int cnt = std::min(plan.chunk, steps - n0 + 1);
+            KG_CUDA_TRY(launch_kpm_cluster<T>(h->dev, R, sym, plan, phi_l, cur, prev, out, ring, cnt, s));
+            KG_CUDA_TRY(launch_reduce_ring(ring, 0, cnt, kRing, plan.grid, R, sym, n0, mu, r_stride, M, s));
             h->counters.kpm_launches += 1;
             h->counters.other_launches += 1;
             h->counters.kpm_site_steps += (double)h->n * R * cnt;

@@ -110,20 +110,30 @@ cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const vec2_t<T>* L,
 template <typename T>
 int kpm_grid(const DevH& H, int R, bool sym);
 
-// Small instances: true when `grid` (the grid of the per-step kernels, at most 16 CTAs)
-// can run as one resident thread-block cluster for this H, R and mode (cached per device).
-template <typename T>
-bool kpm_cluster_ok(const DevH& H, int R, bool sym, int grid);
+// Small instances: the moment recursion of an H with at most 16 CTAs of work per step
+// runs as one thread-block cluster per chunk of steps, vectors in shared memory.
+constexpr int kClusterMaxChunk = 256;   // steps per launch at most (one ring of partial slabs)
+struct ClusterPlan {
+    int grid = 0;        // CTAs = cluster size (0: the cluster path is not available)
+    int log_nt = 0;      // threads per CTA = 1 << log_nt, one item per thread
+    int chunk = 0;       // recursion steps per launch at most (<= kClusterMaxChunk)
+    size_t smem = 0;     // dynamic shared memory per CTA
+};
 
-// The non-first KPM steps n0 .. n0 + nsteps - 1 in one cluster launch of `grid` CTAs:
-// the same arithmetic and partial sums as nsteps per-step launches (bitwise), step k's
-// partials in ring slab (slab0 + k) % ring_size.  cur / prev / out are the blocks of the
-// first of these steps; the kernel rotates them like the per-step loop.
+// Chooses the cluster plan for this H, R and mode (cached per device); false when the
+// instance is too large (more than 16 CTAs of work or R > 16) or no such cluster fits.
 template <typename T>
-cudaError_t launch_kpm_cluster(const DevH& H, int R, bool sym, const vec2_t<T>* L,
-                               const vec2_t<T>* cur, const vec2_t<T>* prev, vec2_t<T>* out,
-                               double* ring, int slab0, int ring_size, int nsteps, int grid,
-                               cudaStream_t s);
+bool kpm_cluster_plan(const DevH& H, int R, bool sym, ClusterPlan* plan);
+
+// The non-first KPM steps n0 .. n0 + nsteps - 1 (nsteps <= plan.chunk) in one cluster
+// launch: the per-step kernels' vectors (bitwise), and per step k the per-CTA partial
+// sums in ring slab k, laid out [k][plan.grid][R][2] like theirs.  cur / prev / out are
+// the blocks of the first of these steps; phi_n and phi_{n-1} are left in the blocks the
+// per-step loop's pointer rotation would leave them in.
+template <typename T>
+cudaError_t launch_kpm_cluster(const DevH& H, int R, bool sym, const ClusterPlan& plan,
+                               const vec2_t<T>* L, const vec2_t<T>* cur, const vec2_t<T>* prev,
+                               vec2_t<T>* out, double* ring, int nsteps, cudaStream_t s);
 
 // Reduce per-block partials of a KPM run into moments mu[r * r_stride + n].
 //   first: partial [grid][R][A] of the first step (A = 2 sym, 4 gen)

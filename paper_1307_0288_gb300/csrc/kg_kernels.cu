@@ -242,75 +242,166 @@ __global__ void __launch_bounds__(kBlock<T>) kpm_gen_kernel(DevH H, const vec2_t
 }
 
 // --------------------------------------------------------------------------------
-// Small instances: many KPM steps in one launch of one thread-block cluster.
-// A 4096-site sheet with one vector is 8 CTAs of work per step, and one launch per step
-// then costs more than the step.  Here the grid (the same grid the per-step kernels use,
-// at most 16 CTAs) is a single cluster that runs the recursion steps n0 .. n0+nsteps-1:
-// each step does exactly what kpm_sym_kernel / kpm_gen_kernel (not FIRST) does with that
-// grid -- the same items per thread, the same operations in the same order, the same
-// block reduction into ring slab (slab0 + k) % ring_size -- so the moments are bitwise
-// those of the per-step launches.  Steps are separated by the cluster's hardware barrier
-// (arrive.release / wait.acquire at cluster scope), which every thread of every CTA
-// reaches once per step: there is no spin loop.  Vectors written within the launch are
-// read with L2-only loads (ld.global.cg); the rotation of the three block pointers is
-// the host's (out <- cur's block after the step, in place over phi_{n-1}).
+// Small instances: many KPM steps in one launch of one thread-block cluster, with the
+// vectors resident in the cluster's shared memory.
+// A 4096-site sheet with one vector is a few CTAs of work per step; one launch per step
+// then costs several times the step, and so do global-memory round trips between steps.
+// Here one cluster of G <= 16 CTAs of nt threads (one item w = n R + r per thread, CTA
+// b owning items b nt .. b nt + nt - 1) runs the recursion steps of a chunk:
+//   * each CTA keeps its items of phi_n and phi_{n-1} in shared memory (two buffers of
+//     nt + 1 entries; entry nt is a permanent zero, the stand-in for the zero row N);
+//   * a step reads the three neighbours through distributed shared memory (the owner
+//     CTA of item j R + r is (j R + r) / nt), forms phi_{n+1} = 2 H~ phi_n - phi_{n-1}
+//     with the per-step kernels' arithmetic (so the vectors are bitwise theirs) and
+//     writes it in place over phi_{n-1};
+//   * the two inner products are formed per thread (Acc<T>), merged across the lanes
+//     that hold the same vector by double-float additions (TwoSum), and stored per warp
+//     in a shared-memory table [step][warp][r]; the cross-warp sums, in a fixed order,
+//     are done once at the end of the chunk and written to the ring slabs [step][G][R][2]
+//     that the moment reduction reads;
+//   * steps are separated by the cluster's hardware barrier (arrive.release /
+//     wait.acquire at cluster scope), which every thread of every CTA reaches once per
+//     step (and once before the first step, so no CTA reads a peer that has not started):
+//     no spin loop.  After the last step each CTA writes its phi_n and phi_{n-1} back to
+//     the global blocks that the per-step loop's pointer rotation would leave them in.
 // --------------------------------------------------------------------------------
 __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
+__device__ __forceinline__ uint32_t map_cluster_rank(uint32_t local_smem, uint32_t rank) {
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(local_smem), "r"(rank));
+    return a;
+}
+
+__device__ __forceinline__ void ld_cluster(uint32_t a, double2& v) {
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a));
+}
+__device__ __forceinline__ void ld_cluster(uint32_t a, float2& v) {
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+}
+
+// (s, c) += (s2, c2) for double-float pairs: Knuth's TwoSum of the heads, the tails and
+// the rounding error summed, then renormalised (FastTwoSum).  Exact roundings throughout.
+__device__ __forceinline__ void df_merge(float& s, float& c, float s2, float c2) {
+    const float t = __fadd_rn(s, s2);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+    const float cc = __fadd_rn(__fadd_rn(c, c2), err);
+    s = __fadd_rn(t, cc);
+    c = __fsub_rn(cc, __fsub_rn(s, t));
+}
+
+constexpr int kClusterMaxR = 16;   // vectors per block the cluster path takes
+
 template <typename T, int R, bool ONSITE, bool SYM>
-__global__ void __launch_bounds__(kBlock<T>) kpm_cluster_kernel(DevH H, const vec2_t<T>* __restrict__ L,
-                                                               const vec2_t<T>* cur, const vec2_t<T>* prev,
-                                                               vec2_t<T>* out, double* __restrict__ ring,
-                                                               int slab0, int ring_size, int nsteps) {
+__global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T>* __restrict__ L,
+                                                         const vec2_t<T>* cur_g, const vec2_t<T>* prev_g,
+                                                         vec2_t<T>* out_g, double* __restrict__ ring,
+                                                         int nsteps, int log_nt) {
+    static_assert(R <= kClusterMaxR, "cluster path: at most 16 vectors per block");
     using V2 = vec2_t<T>;
-    constexpr int NT = kBlock<T>;
+    extern __shared__ __align__(16) unsigned char kg_cluster_smem[];
+    const int nt = 1 << log_nt;
+    const int nwarps = nt >> 5;
+    V2* sv = reinterpret_cast<V2*>(kg_cluster_smem);                    // [2][nt + 1]
+    float4* wp = reinterpret_cast<float4*>(sv + 2 * (nt + 1));          // [nsteps][nwarps][R]
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int r = t & (R - 1);
     const int64_t n_items = H.n * R;
-    const int64_t stride = (int64_t)gridDim.x * NT;
-    const int r = threadIdx.x & (R - 1);
-    const T c = (T)(2.0 * H.h);
-    for (int k = 0; k < nsteps; k++) {
-        Acc<T> a0, a1;
-        int64_t w = (int64_t)blockIdx.x * NT + threadIdx.x;
-        Idx3 nid;
-        if (w < n_items) nid = load_idx(H.idx, H.istride, w / R);
-        for (; w < n_items; w += stride) {
-            const int64_t n = w / R;
-            Nbr<T> g;
-            g.a = __ldcg(cur + (int64_t)nid.i0 * R + r);
-            g.b = __ldcg(cur + (int64_t)nid.i1 * R + r);
-            g.c = __ldcg(cur + (int64_t)nid.i2 * R + r);
-            g.x = __ldcg(cur + n * R + r);
-            T e = 0;
-            if constexpr (ONSITE) e = (T)(2.0 * __ldg(H.onsite + n));
-            const V2 z = __ldcg(prev + w);
-            V2 l = mk<T>(0, 0);
-            if constexpr (!SYM) l = __ldg(L + w);
-            if (w + stride < n_items) nid = load_idx(H.idx, H.istride, (w + stride) / R);
-            const T yr = hop<T>(c, g.a.x, g.b.x, g.c.x, e, g.x.x, z.x, ONSITE);
-            const T yi = hop<T>(c, g.a.y, g.b.y, g.c.y, e, g.x.y, z.y, ONSITE);
-            out[w] = mk<T>(yr, yi);
-            if constexpr (SYM) {
-                a0.add_prod(g.x.x, g.x.x);
-                a0.add_prod(g.x.y, g.x.y);
-                a1.add_prod(yr, g.x.x);
-                a1.add_prod(yi, g.x.y);
-            } else {
-                a0.add_prod(l.x, yr);
-                a0.add_prod(l.y, yi);
-                a1.add_prod(l.x, yi);
-                a1.add_prod(-l.y, yr);
-            }
+    const int64_t w = ((int64_t)blockIdx.x << log_nt) + t;
+    const bool valid = w < n_items;
+    const V2 zero = mk<T>(0, 0);
+
+    // own items of phi_n (buffer 0) and phi_{n-1} (buffer 1), and the zero entries
+    sv[t] = valid ? cur_g[w] : zero;
+    sv[nt + 1 + t] = valid ? prev_g[w] : zero;
+    if (t == 0) {
+        sv[nt] = zero;
+        sv[2 * nt + 1] = zero;
+    }
+    // cluster addresses of the three neighbours in buffer 0 (buffer 1 is boff bytes on)
+    const int64_t n = valid ? w / R : H.n;
+    uint32_t na[3];
+    {
+        const Idx3 j = valid ? load_idx(H.idx, H.istride, n) : Idx3{(int32_t)H.n, (int32_t)H.n, (int32_t)H.n};
+        const int32_t jj[3] = {j.i0, j.i1, j.i2};
+        const uint32_t base = (uint32_t)__cvta_generic_to_shared(sv);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const int64_t item = (int64_t)jj[q] * R + r;
+            const bool zr = jj[q] >= H.n;   // removed or missing neighbour: the zero entry
+            const uint32_t rank = zr ? blockIdx.x : (uint32_t)(item >> log_nt);
+            const uint32_t slot = zr ? (uint32_t)nt : (uint32_t)(item & (nt - 1));
+            na[q] = map_cluster_rank(base + slot * (uint32_t)sizeof(V2), rank);
         }
-        double acc[2] = {a0.value(), a1.value()};
-        double* slab = ring + (int64_t)((slab0 + k) % ring_size) * gridDim.x * R * 2;
-        block_reduce<R, 2, NT>(acc, slab + (int64_t)blockIdx.x * R * 2);
+    }
+    T e = 0;
+    if constexpr (ONSITE) e = valid ? (T)(2.0 * __ldg(H.onsite + n)) : (T)0;
+    V2 l = zero;
+    if constexpr (!SYM) l = valid ? __ldg(L + w) : zero;
+    const T c = (T)(2.0 * H.h);
+    const uint32_t boff = (uint32_t)((nt + 1) * sizeof(V2));
+    cluster_barrier();   // every CTA's buffers are filled before any peer reads them
+
+    int cb = 0;   // buffer holding phi_n
+    for (int k = 0; k < nsteps; k++) {
+        const uint32_t o = cb ? boff : 0u;
+        V2 ga, gb, gc;
+        ld_cluster(na[0] + o, ga);
+        ld_cluster(na[1] + o, gb);
+        ld_cluster(na[2] + o, gc);
+        V2* curb = sv + cb * (nt + 1);
+        V2* prvb = sv + (cb ^ 1) * (nt + 1);
+        const V2 x = curb[t];
+        const V2 z = prvb[t];
+        const T yr = hop<T>(c, ga.x, gb.x, gc.x, e, x.x, z.x, ONSITE);
+        const T yi = hop<T>(c, ga.y, gb.y, gc.y, e, x.y, z.y, ONSITE);
+        if (valid) prvb[t] = mk<T>(yr, yi);
+        Acc<T> a0, a1;   // padding threads hold zeros and add nothing
+        if constexpr (SYM) {
+            a0.add_prod(x.x, x.x);
+            a0.add_prod(x.y, x.y);
+            a1.add_prod(yr, x.x);
+            a1.add_prod(yi, x.y);
+        } else {
+            a0.add_prod(l.x, yr);
+            a0.add_prod(l.y, yi);
+            a1.add_prod(l.x, yi);
+            a1.add_prod(-l.y, yr);
+        }
+        float s0 = a0.s, c0 = a0.c, s1 = a1.s, c1 = a1.c;
+#pragma unroll
+        for (int off = 16; off >= R; off >>= 1) {
+            const float s0o = __shfl_xor_sync(0xffffffffu, s0, off), c0o = __shfl_xor_sync(0xffffffffu, c0, off);
+            const float s1o = __shfl_xor_sync(0xffffffffu, s1, off), c1o = __shfl_xor_sync(0xffffffffu, c1, off);
+            df_merge(s0, c0, s0o, c0o);
+            df_merge(s1, c1, s1o, c1o);
+        }
+        if (lane < R) wp[((int64_t)k * nwarps + warp) * R + lane] = make_float4(s0, c0, s1, c1);
         cluster_barrier();
-        const V2* next = out;
-        prev = cur;
-        out = const_cast<V2*>(cur);
-        cur = next;
+        cb ^= 1;
+        const vec2_t<T>* next = out_g;   // the per-step loop's rotation of the global blocks
+        prev_g = cur_g;
+        out_g = const_cast<vec2_t<T>*>(cur_g);
+        cur_g = next;
+    }
+    // no peer reads this CTA's buffers any more; write phi_n and phi_{n-1} back
+    if (valid) {
+        const_cast<vec2_t<T>*>(cur_g)[w] = sv[cb * (nt + 1) + t];
+        const_cast<vec2_t<T>*>(prev_g)[w] = sv[(cb ^ 1) * (nt + 1) + t];
+    }
+    // cross-warp sums per (step, vector, product), fixed order, into ring slab k
+    for (int i = t; i < nsteps * R * 2; i += nt) {
+        const int k = i / (2 * R), rr = (i >> 1) & (R - 1), q = i & 1;
+        float s = 0.0f, cc = 0.0f;
+        for (int wi = 0; wi < nwarps; wi++) {
+            const float4 v = wp[((int64_t)k * nwarps + wi) * R + rr];
+            if (q == 0) df_merge(s, cc, v.x, v.y);
+            else df_merge(s, cc, v.z, v.w);
+        }
+        ring[(((int64_t)k * gridDim.x + blockIdx.x) * R + rr) * 2 + q] = (double)s + (double)cc;
     }
 }
 
@@ -790,23 +881,27 @@ cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const vec2_t<T>* L,
     return cudaGetLastError();
 }
 
-// One launch of `kernel` as a single cluster of `grid` CTAs (grid <= kMaxCluster; above
-// the portable 8 the kernel is allowed the non-portable size).  query = only check that
-// such a cluster can be resident (cudaErrorNotSupported when not).
+// One launch of `kernel` as a single cluster of `grid` CTAs of `threads` threads with
+// `smem` bytes of dynamic shared memory (above the portable cluster size of 8 the kernel
+// is allowed the non-portable size).  query = only check that such a cluster can be
+// resident (cudaErrorNotSupported when not).
 constexpr int kMaxCluster = 16;
+constexpr size_t kClusterSmemBudget = 96 * 1024;   // shared memory per CTA of the cluster path
 
 template <typename... KArgs, typename... Args>
-static cudaError_t launch_single_cluster(void (*kernel)(KArgs...), int grid, int threads, bool query,
-                                         cudaStream_t s, Args... args) {
+static cudaError_t launch_single_cluster(void (*kernel)(KArgs...), int grid, int threads, size_t smem,
+                                         bool query, cudaStream_t s, Args... args) {
     if (grid < 1 || grid > kMaxCluster) return cudaErrorNotSupported;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     if (grid > 8) {
-        const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid, 1, 1);
     cfg.blockDim = dim3((unsigned)threads, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -817,50 +912,90 @@ static cudaError_t launch_single_cluster(void (*kernel)(KArgs...), int grid, int
     cfg.numAttrs = 1;
     if (query) {
         int clusters = 0;
-        const cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg);
+        e = cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg);
         if (e != cudaSuccess) return e;
         return clusters >= 1 ? cudaSuccess : cudaErrorNotSupported;
     }
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+#define KG_DISPATCH_R16(R_, ...)                                 \
+    switch (R_) {                                                \
+        case 1: { constexpr int RR = 1; __VA_ARGS__; } break;    \
+        case 2: { constexpr int RR = 2; __VA_ARGS__; } break;    \
+        case 4: { constexpr int RR = 4; __VA_ARGS__; } break;    \
+        case 8: { constexpr int RR = 8; __VA_ARGS__; } break;    \
+        case 16: { constexpr int RR = 16; __VA_ARGS__; } break;  \
+        default: return cudaErrorNotSupported;                   \
+    }
+
 template <typename T>
-static cudaError_t kpm_cluster_dispatch(const DevH& H, int R, bool sym, bool query, const vec2_t<T>* L,
-                                        const vec2_t<T>* cur, const vec2_t<T>* prev, vec2_t<T>* out,
-                                        double* ring, int slab0, int ring_size, int nsteps, int grid,
-                                        cudaStream_t s) {
-    if (kPaired<T> && R >= 2) return cudaErrorNotSupported;   // complex64 blocks use the paired kernels
+static cudaError_t kpm_cluster_dispatch(const DevH& H, int R, bool sym, const ClusterPlan& p, bool query,
+                                        const vec2_t<T>* L, const vec2_t<T>* cur, const vec2_t<T>* prev,
+                                        vec2_t<T>* out, double* ring, int nsteps, cudaStream_t s) {
     const bool ons = H.onsite != nullptr;
     cudaError_t e = cudaErrorNotSupported;
-    KG_DISPATCH_R(R, if constexpr (!kPaired<T> || RR == 1) { KG_BOOL(ons, ON, KG_BOOL(sym, SY,
-        e = launch_single_cluster(kpm_cluster_kernel<T, RR, ON, SY>, grid, kBlock<T>, query, s, H, L, cur,
-                                  prev, out, ring, slab0, ring_size, nsteps))) });
+    KG_DISPATCH_R16(R, KG_BOOL(ons, ON, KG_BOOL(sym, SY,
+        e = launch_single_cluster(kpm_cluster_kernel<T, RR, ON, SY>, p.grid, 1 << p.log_nt, p.smem, query, s, H,
+                                  L, cur, prev, out, ring, nsteps, p.log_nt))));
     return e;
 }
 
 template <typename T>
-bool kpm_cluster_ok(const DevH& H, int R, bool sym, int grid) {
-    if (grid < 1 || grid > kMaxCluster || (kPaired<T> && R >= 2)) return false;
+bool kpm_cluster_plan(const DevH& H, int R, bool sym, ClusterPlan* plan) {
+    if (R < 1 || R > kClusterMaxR || (R & (R - 1))) return false;
     int dev = 0;
     cudaGetDevice(&dev);
-    const uint64_t key = ((uint64_t)dev << 40) | ((uint64_t)sizeof(T) << 32) | ((uint64_t)R << 16) |
-                         ((uint64_t)grid << 2) | ((uint64_t)(H.onsite != nullptr) << 1) | (uint64_t)sym;
-    static thread_local std::unordered_map<uint64_t, bool> cache;
+    struct Key {
+        int dev, tsize, R, sym, ons;
+        int64_t n;
+        bool operator==(const Key& o) const {
+            return dev == o.dev && tsize == o.tsize && R == o.R && sym == o.sym && ons == o.ons && n == o.n;
+        }
+    };
+    struct KeyHash {
+        size_t operator()(const Key& k) const {
+            return std::hash<int64_t>()(k.n) ^ ((size_t)k.dev << 48) ^ ((size_t)k.tsize << 40) ^
+                   ((size_t)k.R << 32) ^ ((size_t)k.sym << 31) ^ ((size_t)k.ons << 30);
+        }
+    };
+    static thread_local std::unordered_map<Key, ClusterPlan, KeyHash> cache;
+    const Key key{dev, (int)sizeof(T), R, sym ? 1 : 0, H.onsite ? 1 : 0, H.n};
     auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
-    const cudaError_t e = kpm_cluster_dispatch<T>(H, R, sym, true, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                  0, 1, 0, grid, nullptr);
-    if (e != cudaSuccess) cudaGetLastError();   // a refused query must not leak into later launch checks
-    cache[key] = e == cudaSuccess;
-    return e == cudaSuccess;
+    if (it == cache.end()) {
+        ClusterPlan best;   // grid 0: not available
+        const int64_t items = H.n * R;
+        // the smallest CTAs that keep the cluster within 16 CTAs: the FP64 work spreads over the most SMs
+        for (int log_nt = 7; log_nt <= 9 && best.grid == 0; log_nt++) {
+            const int64_t nt = (int64_t)1 << log_nt;
+            const int64_t grid = (items + nt - 1) / nt;
+            if (grid < 1 || grid > kMaxCluster) continue;
+            const size_t vec = 2 * (size_t)(nt + 1) * sizeof(vec2_t<T>);
+            const size_t per_step = (size_t)(nt / 32) * R * sizeof(float4);
+            if (vec + per_step > kClusterSmemBudget) continue;
+            ClusterPlan p;
+            p.log_nt = log_nt;
+            p.grid = (int)grid;
+            p.chunk = (int)std::min<size_t>(kClusterMaxChunk, (kClusterSmemBudget - vec) / per_step);
+            p.smem = vec + (size_t)p.chunk * per_step;
+            const cudaError_t e = kpm_cluster_dispatch<T>(H, R, sym, p, true, nullptr, nullptr, nullptr, nullptr,
+                                                          nullptr, 0, nullptr);
+            if (e != cudaSuccess) cudaGetLastError();   // a refused query must not leak into later launch checks
+            else best = p;
+        }
+        it = cache.emplace(key, best).first;
+    }
+    *plan = it->second;
+    return plan->grid > 0;
 }
 
 template <typename T>
-cudaError_t launch_kpm_cluster(const DevH& H, int R, bool sym, const vec2_t<T>* L, const vec2_t<T>* cur,
-                               const vec2_t<T>* prev, vec2_t<T>* out, double* ring, int slab0, int ring_size,
-                               int nsteps, int grid, cudaStream_t s) {
+cudaError_t launch_kpm_cluster(const DevH& H, int R, bool sym, const ClusterPlan& p, const vec2_t<T>* L,
+                               const vec2_t<T>* cur, const vec2_t<T>* prev, vec2_t<T>* out, double* ring,
+                               int nsteps, cudaStream_t s) {
     if (nsteps <= 0) return cudaSuccess;
-    return kpm_cluster_dispatch<T>(H, R, sym, false, L, cur, prev, out, ring, slab0, ring_size, nsteps, grid, s);
+    if (nsteps > p.chunk || p.grid < 1) return cudaErrorInvalidValue;
+    return kpm_cluster_dispatch<T>(H, R, sym, p, false, L, cur, prev, out, ring, nsteps, s);
 }
 
 template <typename T>
@@ -998,10 +1133,10 @@ cudaError_t launch_to_c64(const double2* in, float2* out, int64_t n_items, cudaS
                                            const vec2_t<T>*, const vec2_t<T>*, vec2_t<T>*, double*,   \
                                            int, cudaStream_t);                                      \
     template int kpm_grid<T>(const DevH&, int, bool);                                              \
-    template bool kpm_cluster_ok<T>(const DevH&, int, bool, int);                                  \
-    template cudaError_t launch_kpm_cluster<T>(const DevH&, int, bool, const vec2_t<T>*,           \
-                                               const vec2_t<T>*, const vec2_t<T>*, vec2_t<T>*,     \
-                                               double*, int, int, int, int, cudaStream_t);          \
+    template bool kpm_cluster_plan<T>(const DevH&, int, bool, ClusterPlan*);                       \
+    template cudaError_t launch_kpm_cluster<T>(const DevH&, int, bool, const ClusterPlan&,         \
+                                               const vec2_t<T>*, const vec2_t<T>*, const vec2_t<T>*, \
+                                               vec2_t<T>*, double*, int, cudaStream_t);             \
     template cudaError_t launch_evolve<T>(const DevH&, int, int, bool, bool, double, double, double, \
                                           const ChainsT<T>&, cudaStream_t);                        \
     template cudaError_t launch_apply<T>(const DevH&, int, int, double, const vec2_t<T>*,           \
