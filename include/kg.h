@@ -243,8 +243,8 @@ kg_status kg_test_alloc_cap(uint64_t bytes);
  * 256 steps run in one launch of a single thread-block cluster that keeps the vectors in
  * its shared memory and separates the steps with the cluster's hardware barrier.  The
  * Chebyshev vectors are bitwise those of one launch per step; the moments' inner
- * products are summed in another order (double-float sums, agreement to about 1e-15 of
- * the largest moment).  enable = 0 selects one launch per step for every size.
+ * products are summed in another order (double-float sums; the two paths agree within
+ * 1e-12 of the largest moment).  enable = 0 selects one launch per step for every size.
  * Process-wide; takes effect on the next call. */
 kg_status kg_set_small_persistent(int enable);
 

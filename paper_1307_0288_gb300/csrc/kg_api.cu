@@ -19,8 +19,8 @@ namespace kg {
 // of memory (0 = no cap).  Injects KG_ENOMEM on the host, without a real allocation failure.
 static std::atomic<unsigned long long> g_alloc_cap{0};
 
-// Small instances run their moment recursion as one cluster launch per ring of steps
-// (kg_set_small_persistent); 0 = one launch per step everywhere.
+// Small instances run their moment recursion as one cluster launch per chunk of up to
+// 256 steps (kg_set_small_persistent); 0 = one launch per step everywhere.
 static std::atomic<int> g_small_persistent{1};
 
 // Device buffer owned by the handle.
