@@ -126,8 +126,8 @@ kg_status kg_lattice_neighbors(const kg_lattice* lattice, const int64_t* vacanci
  * magnitude in [2^-63, 2^63) (random-phase vectors and their Chebyshev iterates are
  * O(1)); smaller entries contribute less accurately (nothing below 2^-126), and larger
  * ones overflow.  Every entry point that returns moments checks them and fails with
- * KG_ENUMERIC when one is NaN or infinite (NaN/Inf inputs, or entries >= 2^63), except
- * kg_dos_moments_noalloc, which runs asynchronously and does not check. */
+ * KG_ENUMERIC when one is NaN or infinite (NaN/Inf inputs, or entries >= 2^63);
+ * kg_dos_moments_noalloc included (it returns after its stream completes). */
 
 typedef struct {
     int32_t n_moments;   /* M >= 1: moments C_0 .. C_{M-1} (Eqs. 32-34) */
@@ -304,10 +304,19 @@ kg_status kg_mlp_gemm_test(const void* a_dev, const void* b_dev, int64_t rows, i
  *   idx_dev     device int32 [3][N], the neighbour table of kg_lattice_neighbors
  *               (slot-major, -1 where absent).
  *   onsite_dev  device double [N], scaled on-site energies eps_n / E_max, or NULL.
+ *               Precondition: 3|hopping| + max_n |onsite_n| < 1, so that the spectrum
+ *               of H~ lies inside [-1, 1] (Eqs. 32-34); checked on the device before the
+ *               recursion, KG_EINVAL otherwise.  kg_build_hamiltonian sets the on-site
+ *               energy of removed sites to 0; pass 0 there too.  (When phi is 0 on the
+ *               removed sites, as the random-phase vectors of Sec. 3.1.1 are, the value
+ *               there does not enter the moments; a nonzero phi entry on a removed
+ *               site would add a spurious delta(E - eps_n) term.)
  *   n_sites     N.   hopping: the scaled hopping -gamma0 / E_max (0 < |h| < 1/3).
  *   n_vectors   R, a power of two in 1..64.   n_moments: M >= 1.
  *   phi_dev     device [N][R][2] random vectors;  mu_dev: device [R][M][2] output.
  *   cuda_stream stream the work is issued on; the call returns after it completes.
+ *               The caller's tensors are neither freed nor kept.  Moments that are
+ *               NaN or infinite give KG_ENUMERIC.
  * Scratch needed: 12 N + 48 (N + 1) R bytes plus about 0.5 MB x R of partial sums;
  * larger problems are rejected with KG_EINVAL and a message giving both sizes.
  * The first call on a device looks up the array's device address (with that device

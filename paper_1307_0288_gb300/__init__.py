@@ -365,14 +365,52 @@ def evolve(h: Hamiltonian, dt: float, which: int, x, out, bessel_tol: float = 1e
     return out
 
 
+def _noalloc_args(idx_dev, onsite_dev, n_sites: int, phi_dev, mu_dev):
+    """Checks the tensors of dos_moments_noalloc before any pointer reaches the
+    library, which cannot see buffer sizes: a short or mistyped buffer there would be
+    read or written out of bounds on the GPU.  Shapes and dtypes are checked first,
+    then that every tensor is a contiguous CUDA tensor on the current device.
+    Returns (R, M).  Raises ValueError."""
+    import torch
+    n = int(n_sites)
+    if n < 1:
+        raise ValueError("n_sites must be >= 1")
+    if idx_dev.dtype != torch.int32 or tuple(idx_dev.shape) not in ((3, n), (3 * n,)):
+        raise ValueError(f"idx_dev must be int32 [3][N] with N = {n}, got {idx_dev.dtype} {tuple(idx_dev.shape)}")
+    if onsite_dev is not None and (onsite_dev.dtype != torch.float64 or tuple(onsite_dev.shape) != (n,)):
+        raise ValueError(f"onsite_dev must be float64 [N] with N = {n}, got {onsite_dev.dtype} "
+                         f"{tuple(onsite_dev.shape)}")
+    if phi_dev.dtype != torch.complex128 or phi_dev.dim() not in (1, 2) or phi_dev.shape[0] != n:
+        raise ValueError(f"phi_dev must be complex128 [N] or [N][R] with N = {n}, got {phi_dev.dtype} "
+                         f"{tuple(phi_dev.shape)}")
+    r = 1 if phi_dev.dim() == 1 else int(phi_dev.shape[1])
+    if mu_dev.dtype != torch.complex128 or mu_dev.dim() != 2 or mu_dev.shape[0] != r or mu_dev.shape[1] < 1:
+        raise ValueError(f"mu_dev must be complex128 [R][M] with R = {r} (the vectors of phi_dev), got "
+                         f"{mu_dev.dtype} {tuple(mu_dev.shape)}")
+    tensors = [("idx_dev", idx_dev), ("phi_dev", phi_dev), ("mu_dev", mu_dev)]
+    if onsite_dev is not None:
+        tensors.append(("onsite_dev", onsite_dev))
+    for name, t in tensors:
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    dev = torch.cuda.current_device()
+    for name, t in tensors:
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+    return r, int(mu_dev.shape[1])
+
+
 def dos_moments_noalloc(idx_dev, onsite_dev, n_sites: int, hopping: float, phi_dev, mu_dev,
                         stream=None):
     """kg_dos_moments_noalloc on caller-owned device tensors (no device allocation).
 
-    idx_dev int32 [3][N] (-1 = absent), onsite_dev float64 [N] (eps/E_max) or None,
-    phi_dev complex128 [N] or [N][R], mu_dev complex128 [R][M] (written)."""
-    r = _nvec(phi_dev, n_sites)
-    m = int(mu_dev.shape[-1])
+    idx_dev int32 [3][N] (-1 = absent), onsite_dev float64 [N] (eps/E_max, 0 on removed
+    sites) or None, phi_dev complex128 [N] or [N][R], mu_dev complex128 [R][M] (written).
+    Every tensor must be contiguous and on the current CUDA device (ValueError
+    otherwise)."""
+    r, m = _noalloc_args(idx_dev, onsite_dev, n_sites, phi_dev, mu_dev)
     s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
     _check(lib().kg_dos_moments_noalloc(
         ctypes.c_void_p(idx_dev.data_ptr()),

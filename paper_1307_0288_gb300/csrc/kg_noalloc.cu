@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <string>
 
@@ -57,6 +58,20 @@ __global__ void sentinel_kernel(const int32_t* __restrict__ in, int32_t* __restr
     }
 }
 
+// max |onsite[k]| over k < n as the bit pattern of a non-negative double (which orders
+// like the value), NaN counted as +infinity; *out must start at 0.
+__global__ void onsite_absmax_kernel(const double* __restrict__ onsite, int64_t n,
+                                     unsigned long long* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double m = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const double a = fabs(onsite[k]);
+        m = (a == a) ? fmax(m, a) : INFINITY;
+    }
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace kg
@@ -83,7 +98,8 @@ extern "C" kg_status kg_dos_moments_noalloc(const int32_t* idx_dev, const double
     const size_t b_vec = align256((size_t)(n + 1) * R * sizeof(double2));
     const size_t b_first = align256((size_t)grid * R * 4 * sizeof(double));
     const size_t b_ring = align256((size_t)kNoallocRing * grid * R * 2 * sizeof(double));
-    const size_t need = b_idx + 3 * b_vec + b_first + b_ring;
+    const size_t b_check = 256;   // max |onsite| and the non-finite flag
+    const size_t need = b_idx + 3 * b_vec + b_first + b_ring + b_check;
     if (need > KG_NOALLOC_SCRATCH_BYTES)
         return fail(KG_EINVAL, "kg_dos_moments_noalloc: n_sites x n_vectors too large for the fixed scratch (" +
                                    std::to_string(need) + " bytes needed, " +
@@ -97,6 +113,25 @@ extern "C" kg_status kg_dos_moments_noalloc(const int32_t* idx_dev, const double
     double2* b1 = (double2*)(p + b_idx + 2 * b_vec);
     double* first = (double*)(p + b_idx + 3 * b_vec);
     double* ring = (double*)(p + b_idx + 3 * b_vec + b_first);
+    unsigned long long* onsite_max = (unsigned long long*)(p + b_idx + 3 * b_vec + b_first + b_ring);
+    int* bad_flag = (int*)(onsite_max + 1);
+
+    // The Chebyshev expansion needs the spectrum of H~ inside [-1, 1] (Eqs. 32-34); by
+    // Gershgorin's theorem 3|h| + max|eps_n / E_max| < 1 guarantees it.
+    if (onsite_dev) {
+        KG_CUDA_TRY(cudaMemsetAsync(onsite_max, 0, sizeof(*onsite_max), s));
+        onsite_absmax_kernel<<<stream_grid(n), 256, 0, s>>>(onsite_dev, n, onsite_max);
+        KG_CUDA_TRY(cudaGetLastError());
+        unsigned long long bits = 0;
+        KG_CUDA_TRY(cudaMemcpyAsync(&bits, onsite_max, sizeof(bits), cudaMemcpyDeviceToHost, s));
+        KG_CUDA_TRY(cudaStreamSynchronize(s));
+        double emax_onsite = 0.0;
+        std::memcpy(&emax_onsite, &bits, sizeof(emax_onsite));
+        if (!(3.0 * std::fabs(hopping) + emax_onsite < 1.0))
+            return fail(KG_EINVAL, "kg_dos_moments_noalloc: 3|hopping| + max|onsite| = " +
+                                       std::to_string(3.0 * std::fabs(hopping) + emax_onsite) +
+                                       " must be < 1 (the spectrum of H~ must lie inside [-1, 1])");
+    }
 
     DevH H;
     H.idx = idx;
@@ -135,6 +170,14 @@ extern "C" kg_status kg_dos_moments_noalloc(const int32_t* idx_dev, const double
         out = const_cast<double2*>(cur);
         cur = nc;
     }
+    // moments that are NaN or infinite (non-finite inputs, or entries beyond 2^63) fail
+    KG_CUDA_TRY(cudaMemsetAsync(bad_flag, 0, sizeof(int), s));
+    KG_CUDA_TRY(launch_nonfinite(mu_dev, (int64_t)R * M * 2, bad_flag, s));
+    int bad = 0;
+    KG_CUDA_TRY(cudaMemcpyAsync(&bad, bad_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     KG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad)
+        return fail(KG_ENUMERIC, "kg_dos_moments_noalloc: non-finite moments (NaN/Inf inputs, or vector "
+                                 "entries of magnitude 2^63 or more)");
     return KG_OK;
 }

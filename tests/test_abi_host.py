@@ -148,3 +148,38 @@ def test_ballistic_sigma_sc_and_pade_match_oracle():
     r2 = np.sum((post.pade_value(p2, t2) - y2) ** 2)
     assert r1 <= r2 * (1 + 1e-6)
     assert np.allclose(post.pade_value(p1, t2), post.pade_value(p2, t2), rtol=1e-4)
+
+
+def test_noalloc_binding_rejects_mismatched_buffers_before_the_library():
+    """dos_moments_noalloc hands raw device pointers to a C entry point that cannot see
+    buffer sizes, so the binding checks every tensor first: a short mu, an int64 or
+    transposed neighbour table, a wrong dtype, or a host tensor raises ValueError
+    (on a CPU-only machine, before any library call)."""
+    torch = pytest.importorskip("torch")
+    n, r, m = 64, 2, 16
+    idx = torch.zeros((3, n), dtype=torch.int32)
+    onsite = torch.zeros(n, dtype=torch.float64)
+    phi = torch.zeros((n, r), dtype=torch.complex128)
+    mu = torch.zeros((r, m), dtype=torch.complex128)
+    bad = [
+        dict(mu_dev=torch.zeros((r - 1, m), dtype=torch.complex128)),   # fewer rows than vectors
+        dict(mu_dev=torch.zeros((r, m), dtype=torch.complex64)),
+        dict(idx_dev=torch.zeros((3, n), dtype=torch.int64)),
+        dict(idx_dev=torch.zeros((n, 3), dtype=torch.int32)),
+        dict(idx_dev=torch.zeros((3, n - 1), dtype=torch.int32)),
+        dict(onsite_dev=torch.zeros(n - 1, dtype=torch.float64)),
+        dict(onsite_dev=torch.zeros(n, dtype=torch.float32)),
+        dict(phi_dev=torch.zeros((n + 1, r), dtype=torch.complex128)),
+        dict(phi_dev=torch.zeros((n, r), dtype=torch.float64)),
+    ]
+    for change in bad:
+        args = dict(idx_dev=idx, onsite_dev=onsite, phi_dev=phi, mu_dev=mu)
+        args.update(change)
+        with pytest.raises(ValueError):
+            kg.dos_moments_noalloc(args["idx_dev"], args["onsite_dev"], n, -0.3, args["phi_dev"],
+                                   args["mu_dev"])
+    # right shapes, but host tensors (or a non-contiguous view): still refused
+    with pytest.raises(ValueError, match="CUDA|contiguous"):
+        kg.dos_moments_noalloc(idx, onsite, n, -0.3, phi, mu)
+    with pytest.raises(ValueError):
+        kg.dos_moments_noalloc(idx, onsite, n, -0.3, phi, torch.zeros((m, r), dtype=torch.complex128).t())

@@ -59,3 +59,27 @@ def test_noalloc_rejects_problems_beyond_the_fixed_scratch():
     with pytest.raises(kg.KgError) as e:
         kg.dos_moments_noalloc(idx, None, n, -2.7 / 8.505, phi, mu)
     assert e.value.status == -1 and "scratch" in str(e.value)
+
+
+def test_noalloc_onsite_on_removed_sites_and_the_spectral_bound():
+    """Raw Anderson energies left on the removed sites give the same moments when phi
+    is zero there (the removed rows have no bonds, so they stay zero); on-site energies
+    that push the spectrum of H~ outside [-1, 1] are refused with KG_EINVAL."""
+    w = ki.sheet_cells(24, 16, vacancy_conc=0.03, anderson_w_ev=1.5, lattice_seed=33)
+    phi = w.vectors(2)
+    assert np.all(phi[w.vacancy_mask() > 0] == 0)
+    h = kg.from_workload(w)
+    ref = kg.dos_moments(h, phi, 200)
+    idx = torch.from_numpy(kg.lattice_neighbors(w.kind, w.nx, w.ny, w.vacancies)).to("cuda")
+    raw = torch.from_numpy(np.ascontiguousarray(w.onsite / w.emax_ev)).to("cuda")
+    assert float(raw[torch.from_numpy(w.vacancy_mask() > 0).to("cuda")].abs().max()) > 0
+    phi_dev = torch.from_numpy(np.ascontiguousarray(phi)).to("cuda")
+    mu = torch.zeros((2, 200), dtype=torch.complex128, device="cuda")
+    kg.dos_moments_noalloc(idx, raw, w.n_sites, -w.gamma0_ev / w.emax_ev, phi_dev, mu)
+    got = mu.cpu().numpy()
+    for k in range(2):
+        assert _rel(got[k], ref[k]) < TOL_MOMENTS
+    too_large = raw * 0 + 0.2   # 3 * 2.7 / E_max + 0.2 = 1.07 > 1
+    with pytest.raises(kg.KgError) as e:
+        kg.dos_moments_noalloc(idx, too_large, w.n_sites, -w.gamma0_ev / w.emax_ev, phi_dev, mu)
+    assert e.value.status == -1 and "inside [-1, 1]" in str(e.value)
