@@ -112,6 +112,38 @@ kg_status kg_lattice_neighbors(const kg_lattice* lattice, const int64_t* vacanci
                                int64_t n_vacancies, int32_t* idx_out);
 
 /* ------------------------------------------------------------------------- */
+/* Seeded synthetic inputs (host only, no GPU needed)                         */
+/* ------------------------------------------------------------------------- */
+/* The random numbers the method draws (Sec. 2: random single vacancies; Anderson
+ * on-site energies uniform in [-W/2, W/2]; Sec. 3.1.1: random-phase vectors
+ * phi_n = exp(i theta_n), theta_n uniform in [0, 2 pi)), from SplitMix64 (Steele, Lea
+ * and Flood, OOPSLA 2014) in counter mode: key = mix64(seed + stream G),
+ * x_k = mix64(key + (k + 1) G), G = 0x9E3779B97F4A7C15, arithmetic modulo 2^64;
+ * uniform u_k = (x_k >> 11) 2^-53.  Streams: 0 vacancies, 1 Anderson energies, 16 + r
+ * random vector r.  With these a C caller builds the same seeded workloads as the
+ * Python input module: kg_n_vacancies -> kg_vacancy_sites -> kg_anderson_onsite ->
+ * kg_build_hamiltonian, then kg_random_phase_vectors -> kg_dos_moments / kg_vac /
+ * kg_msd.  Words, vacancy sites, energies and phases are bit-identical to that module;
+ * cos and sin are the C library's.  All buffers are host memory, caller-owned;
+ * errors: KG_EINVAL. */
+
+/* SplitMix64 words x_start .. x_start + count - 1 of one stream into out[count]. */
+kg_status kg_splitmix64(uint64_t seed, uint64_t stream, int64_t start, int64_t count, uint64_t* out);
+/* N_v = round(n N), rounded half to even, for a concentration 0 <= n <= 1. */
+kg_status kg_n_vacancies(int64_t n_sites, double concentration, int64_t* n_vac);
+/* n_vac distinct sites of [0, N) (N < 2^31 - 1), sorted ascending, into out[n_vac]: a partial
+ * Fisher-Yates shuffle whose step k swaps positions k and k + floor(w_k (N - k) / 2^32),
+ * w_k the top 32 bits of word k of stream 0. */
+kg_status kg_vacancy_sites(int64_t n_sites, int64_t n_vac, uint64_t seed, int64_t* out);
+/* out_ev[n] = W (u_n - 1/2) in eV from stream 1, n < N. */
+kg_status kg_anderson_onsite(int64_t n_sites, double w_ev, uint64_t seed, double* out_ev);
+/* out [N][R][2] (interleaved complex, site-major as the moment entry points take it):
+ * phi_n^(r) = (cos theta, sin theta), theta = 2 pi u_n of stream 16 + r, and 0 on the
+ * n_vacancies removed sites (in [0, N)). */
+kg_status kg_random_phase_vectors(int64_t n_sites, int n_vectors, uint64_t seed, const int64_t* vacancies,
+                                  int64_t n_vacancies, double* out);
+
+/* ------------------------------------------------------------------------- */
 /* Moments and time evolution on the GPU                                      */
 /* ------------------------------------------------------------------------- */
 
@@ -346,6 +378,16 @@ typedef struct {
 kg_status kg_timing_enable(kg_hamiltonian* h, int enable);
 /* Reads the counters accumulated since the last kg_timing_enable (synchronises). */
 kg_status kg_timing_read(kg_hamiltonian* h, kg_timing* out);
+
+/* Measured FP64 fused multiply-add throughput of the current device (not in the paper:
+ * the denominator of the FP64 recursion's ALU roofline).  Runs `repeats` (1..100)
+ * launches of a kernel in which every thread of four 256-thread CTAs per SM advances
+ * eight independent FP64 FMA chains for a fixed number of iterations (no waits, no
+ * memory traffic beyond one store per thread), each timed with CUDA events; writes the
+ * best rate in FMA instructions per second (thread-level: one DFMA = 2 flops) to
+ * *fma_per_s.  Allocates and frees a small device buffer; synchronous.
+ * Errors: KG_EINVAL (repeats out of range, null output), KG_ECUDA. */
+kg_status kg_fp64_fma_rate(int repeats, double* fma_per_s);
 
 /* ------------------------------------------------------------------------- */
 /* Host-side helpers (FP64, no GPU needed)                                    */

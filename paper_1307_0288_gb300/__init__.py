@@ -72,6 +72,12 @@ ABI = [
     ("kg_evolve", _I, [_P, _D, _I, _D, _P, _P, _I]),
     ("kg_timing_enable", _I, [_P, _I]),
     ("kg_timing_read", _I, [_P, ctypes.POINTER(_Timing)]),
+    ("kg_fp64_fma_rate", _I, [_I, ctypes.POINTER(_D)]),
+    ("kg_splitmix64", _I, [ctypes.c_uint64, ctypes.c_uint64, _I64, _I64, _P]),
+    ("kg_n_vacancies", _I, [_I64, _D, ctypes.POINTER(_I64)]),
+    ("kg_vacancy_sites", _I, [_I64, _I64, ctypes.c_uint64, _P]),
+    ("kg_anderson_onsite", _I, [_I64, _D, ctypes.c_uint64, _P]),
+    ("kg_random_phase_vectors", _I, [_I64, _I, ctypes.c_uint64, _P, _I64, _P]),
     ("kg_bessel_series", _I, [_D, _D, _I, _P, ctypes.POINTER(_I)]),
     ("kg_jackson", _I, [_I, _P]),
     ("kg_kpm_sum", _I, [_P, _I, _I, _P, _I, _D, _D, _P]),
@@ -400,6 +406,57 @@ def _noalloc_args(idx_dev, onsite_dev, n_sites: int, phi_dev, mu_dev):
         if t.device.index != dev:
             raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
     return r, int(mu_dev.shape[1])
+
+
+# ----------------------------------------------------------------- seeded inputs
+
+def splitmix64(seed: int, stream: int, count: int, start: int = 0) -> np.ndarray:
+    """kg_splitmix64: counter-mode SplitMix64 words x_start .. x_{start+count-1}."""
+    out = np.zeros(int(count), dtype=np.uint64)
+    _check(lib().kg_splitmix64(int(seed) % 2**64, int(stream) % 2**64, int(start), int(count),
+                               ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def n_vacancies(n_sites: int, concentration: float) -> int:
+    """kg_n_vacancies: round(n N), half to even."""
+    v = ctypes.c_int64()
+    _check(lib().kg_n_vacancies(int(n_sites), float(concentration), ctypes.byref(v)))
+    return v.value
+
+
+def vacancy_sites(n_sites: int, n_vac: int, seed: int) -> np.ndarray:
+    """kg_vacancy_sites: n_vac distinct removed sites, sorted (int64)."""
+    out = np.zeros(int(n_vac), dtype=np.int64)
+    _check(lib().kg_vacancy_sites(int(n_sites), int(n_vac), int(seed) % 2**64,
+                                  ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def anderson_onsite(n_sites: int, w_ev: float, seed: int) -> np.ndarray:
+    """kg_anderson_onsite: eps_n = W (u_n - 1/2) eV."""
+    out = np.zeros(int(n_sites), dtype=np.float64)
+    _check(lib().kg_anderson_onsite(int(n_sites), float(w_ev), int(seed) % 2**64,
+                                    ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def random_phase_vectors(n_sites: int, n_vec: int, seed: int, vacancies=None) -> np.ndarray:
+    """kg_random_phase_vectors -> complex128 [N][R], zero on the removed sites."""
+    vac = np.ascontiguousarray(np.zeros(0, dtype=np.int64) if vacancies is None else vacancies, dtype=np.int64)
+    out = np.zeros((int(n_sites), int(n_vec)), dtype=np.complex128)
+    _check(lib().kg_random_phase_vectors(int(n_sites), int(n_vec), int(seed) % 2**64,
+                                         ctypes.c_void_p(vac.ctypes.data) if vac.size else None, int(vac.size),
+                                         ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def fp64_fma_rate(repeats: int = 5) -> float:
+    """kg_fp64_fma_rate: measured FP64 FMA instructions per second of the current
+    device (best of ``repeats`` timed probe launches)."""
+    v = ctypes.c_double()
+    _check(lib().kg_fp64_fma_rate(int(repeats), ctypes.byref(v)))
+    return v.value
 
 
 def dos_moments_noalloc(idx_dev, onsite_dev, n_sites: int, hopping: float, phi_dev, mu_dev,

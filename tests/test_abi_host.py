@@ -183,3 +183,29 @@ def test_noalloc_binding_rejects_mismatched_buffers_before_the_library():
         kg.dos_moments_noalloc(idx, onsite, n, -0.3, phi, mu)
     with pytest.raises(ValueError):
         kg.dos_moments_noalloc(idx, onsite, n, -0.3, phi, torch.zeros((m, r), dtype=torch.complex128).t())
+
+
+def test_seeded_inputs_from_the_c_abi_match_the_input_module():
+    """The library's SplitMix64 input generators (kg_splitmix64, kg_n_vacancies,
+    kg_vacancy_sites, kg_anderson_onsite, kg_random_phase_vectors) reproduce the Python
+    input module: words, vacancy sites, Anderson energies and the phases bit for bit,
+    the cos/sin of the phases within one unit in the last place (both call the C
+    library here; exact when the platform's numpy and libm agree)."""
+    for seed, stream in [(20130701, 0), (1000, 16), (2**64 - 1, 5)]:
+        assert np.array_equal(kg.splitmix64(seed, stream, 1000, start=7),
+                              ki.splitmix64(seed, stream, 1000, start=7))
+    for n, conc in [(4096, 0.01), (2097152, 0.005), (1000, 0.0025), (10, 0.05)]:
+        assert kg.n_vacancies(n, conc) == ki.n_vacancies(n, conc)
+    for w in [ki.sheet_cells(32, 32, vacancy_conc=0.01), ki.zgnr(20, 100, vacancy_conc=0.02, lattice_seed=9),
+              ki.sheet_cells(64, 32, vacancy_conc=0.005, anderson_w_ev=1.5, lattice_seed=3, vector_seed=77)]:
+        nv = kg.n_vacancies(w.n_sites, w.vacancy_conc)
+        vac = kg.vacancy_sites(w.n_sites, nv, w.lattice_seed)
+        assert np.array_equal(vac, w.vacancies)
+        if w.anderson_w_ev > 0:
+            assert np.array_equal(kg.anderson_onsite(w.n_sites, w.anderson_w_ev, w.lattice_seed), w.onsite)
+        got = kg.random_phase_vectors(w.n_sites, 3, w.vector_seed, vac)
+        want = w.vectors(3)
+        ulp = np.spacing(np.maximum(np.abs(want.real), np.abs(want.imag)).max(initial=1.0))
+        assert np.max(np.abs(got - want)) <= ulp
+        assert np.all(got[vac] == 0)
+        print(f"{w.n_sites} sites: phase vectors bit-identical: {np.array_equal(got, want)}")
