@@ -9,11 +9,19 @@ Algorithm 3: xi <- U(dt)xi + [X,U(dt)]psi, psi <- U(dt)psi (Eq. 44), then the M
 moments of xi (Algorithm 5).  K steps = one kg_msd call with N_c = K + 1 (t_0 is
 free: [X, U(0)] = 0).  The working set (8 vector blocks of 134 MB) exceeds L2.
 
-Metric: Chebyshev site-updates/s, counted as the paper's algorithms define the work
-of a step (per vector: M - 1 moment recursions + 4 (N_p - 1) propagator recursions:
-U(dt)xi, U(dt)psi and the two chains of [X, U(dt)]psi), over all GPUs.  The
-library does less recursion work for the same result (moment doubling, shared
-chains); the executed count is reported separately.
+Metric: Chebyshev site-updates/s executed, one update = one (site, vector, recursion
+step) that a kernel performs (the moment loop runs M/2 doubling steps; the
+propagator runs one step per Bessel term on the chains U(dt)xi, U(dt)psi and
+[X, U(dt)]psi), over all GPUs.  The paper's algorithms do more recursion steps for
+the same result (per vector M - 1 moment steps and 4 (N_p - 1) propagator steps);
+that count over the same time is reported beside it as
+paper_equivalent_site_updates_per_s, a time-to-solution figure.
+
+The roofline denominator of the FP64 step, the device's FP64 FMA rate, is measured in
+the run (kg_fp64_fma_rate) before the timed region.  The line also carries a
+complex64 record: the same K correlation times with complex64 recursion vectors
+(FP64 moments and sums), its time, and the relative error of its sigma^E1(E, t) on
+201 energies against the timed FP64 run's.
 
 --impl reference times the CPU oracle on the host cores on a bounded sample.
 """
@@ -49,7 +57,7 @@ SMALL_WORKLOAD = "vac-sheet-64x64-vac1pct-R1-M512-Nc10-dt1"
 CELLS, VAC, R, M, DT, PREC = WORKLOADS[DEFAULT_WORKLOAD]
 METRIC = "Chebyshev site-updates/s and HBM GB/s vs peak; σ(E,t) time at 1e-5 err vs FP64"
 UNIT = "site-updates/s"
-FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (profiling recipe table); DFMA probe measured 1.20
+FP64_NOMINAL_TFLOPS = 1.25   # nominal GB300 FP64 (profiling recipe table), for context only
 # FP64 work of one doubling-KPM site-vector update on the DP pipe: the recursion
 # y = c (a + b + d) - z costs 3 FMA per real component, 6 FMA = 12 flops per complex item.
 # The two inner products per item are double-float sums on the FP32 pipe.
@@ -97,6 +105,12 @@ def _profiled_traffic(kernel_files, profile: str, n_sites: int = 0):
         return traffic
     except (KeyError, ValueError):
         return None
+
+
+def fp64_peak_tflops(kg):
+    """FP64 peak measured in this run: the library's FMA probe (best of 5 launches),
+    2 flops per FMA."""
+    return 2.0 * kg.fp64_fma_rate(5) / 1e12
 
 
 def _peaks():
@@ -291,6 +305,8 @@ def run_ours(args):
     K, W = args.steps, args.warmup
     prec = kg.KG_C64 if PREC == "c64" else kg.KG_FP64
 
+    fp64_peak = fp64_peak_tflops(kg)
+
     # warm-up: W correlation times
     out_w = torch.zeros((R, W + 1, M), dtype=torch.complex128, device="cuda")
     kg.msd(h, phi_dev, M, W + 1, DT, bessel_tol=TOL, out=out_w, precision=prec)
@@ -354,13 +370,53 @@ def run_ours(args):
         sigma["rel_err_vs_fp64_gpu"] = float(np.max(np.abs(sig - sig64)) / np.max(np.abs(sig64)))
         sigma["fp64_gpu_time_s"] = f64_s + sums_s
 
+    # complex64 record: the same K correlation times on the same inputs with complex64
+    # recursion vectors, timed on the library's stream; its sigma^E1 against the FP64 one
+    c64 = None
+    if PREC == "f64":
+        out_c = torch.zeros((R, K + 1, M), dtype=torch.complex128, device="cuda")
+        warm_c = torch.zeros((R, 2, M), dtype=torch.complex128, device="cuda")
+        kg.msd(h, phi_dev, M, 2, DT, bessel_tol=TOL, out=warm_c, precision=kg.KG_C64)
+        torch.cuda.synchronize()
+        kg.timing_enable(h, True)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        kg.msd(h, phi_dev, M, K + 1, DT, bessel_tol=TOL, out=out_c, precision=kg.KG_C64)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        c_ms = c0.elapsed_time(c1)
+        ccnt = kg.timing_read(h)
+        kg.timing_enable(h, False)
+        t0 = time.perf_counter()
+        sig_c = sigma_e1(out_c.cpu().numpy())
+        c_sums_s = time.perf_counter() - t0
+        c_launch_ms = ccnt["kpm_ms"] / max(ccnt["kpm_launches"], 1)
+        c_bytes = w.n_sites * (12 + 3 * 8 * R)
+        c_gbs = c_bytes / (c_launch_ms * 1e-3) / 1e9
+        c64 = {"precision": "complex64 recursion vectors; FP64 Bessel/Jackson coefficients, moments "
+                            "and time integration",
+               "times": K + 1, "ms_per_step": c_ms / K, "fp64_ms_per_step": ms / K,
+               "speedup_vs_fp64": ms / c_ms,
+               "sigma_time_s": c_ms * 1e-3 + c_sums_s, "fp64_sigma_time_s": ms * 1e-3 + sums_s,
+               "sigma_rel_err_vs_fp64_gpu": float(np.max(np.abs(sig_c - sig)) / np.max(np.abs(sig))),
+               "sigma_norm": "max over 201 energies and K + 1 times of |sigma_c64 - sigma_fp64| / "
+                             "max |sigma_fp64| (sigma^E1, Eq. 9)",
+               "executed_site_updates_per_s": (ccnt["kpm_site_steps"] + ccnt["evolve_site_steps"]) * world
+               / (c_ms * 1e-3),
+               "kpm_kernel": "kpm_sym_pair_kernel<4> (complex64 doubling KPM step)",
+               "kpm_avg_launch_ms": c_launch_ms, "kpm_achieved_gbs": c_gbs,
+               "kpm_hbm_frac": c_gbs / _peaks().get("hbm_gbs", 6800.0),
+               "kpm_algorithmic_bytes": c_bytes}
+
     # sanity: the moments are finite and bounded by C_0 (|T_n| <= 1)
     c = out[:, 1:].real
     ok = bool(torch.isfinite(c).all()) and bool((c.abs() <= c[..., :1] * (1 + 1e-9) + 1e-300).all())
 
-    work = paper_work_per_step(w.n_sites, R, M, n_p) * K * world
-    value = work / (ms * 1e-3)
-    executed = (cnt["kpm_site_steps"] + cnt["evolve_site_steps"]) * world / (ms * 1e-3)
+    paper_work = paper_work_per_step(w.n_sites, R, M, n_p) * K * world
+    paper_value = paper_work / (ms * 1e-3)
+    executed_work = (cnt["kpm_site_steps"] + cnt["evolve_site_steps"]) * world
+    value = executed_work / (ms * 1e-3)
     kpm_launch_ms = cnt["kpm_ms"] / max(cnt["kpm_launches"], 1)
     flops_per_launch = KPM_FP64_FLOPS_PER_ITEM * w.n_sites * R
     achieved_tflops = flops_per_launch / (kpm_launch_ms * 1e-3) / 1e12
@@ -372,11 +428,13 @@ def run_ours(args):
     hbm_src = "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback"
     if PREC == "f64":
         roofline = {"bound": "alu", "kernel": "kpm_sym_kernel<double> (FP64 doubling KPM step, 6 DFMA per site-vector)",
-                    "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                    "achieved": achieved_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": achieved_tflops / fp64_peak,
                     "traffic": _profiled_traffic(KPM_SOURCES, "kpm_sym_kernel_msd_sheet_2M.md"),
                     "algorithmic_bytes": bytes_per_launch,
-                    "peak_source": "nominal FP64 of the profiling recipe (DFMA probe: 1.20)",
+                    "peak_source": "measured in-run: kg_fp64_fma_rate (8 independent FP64 FMA chains per "
+                                   "thread, 4 x 256-thread CTAs per SM, best of 5 launches), 2 flops per FMA",
+                    "peak_nominal": FP64_NOMINAL_TFLOPS,
                     "avg_launch_ms": kpm_launch_ms,
                     "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak,
                             "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}}
@@ -393,21 +451,26 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": PREC, "data": "synthetic",
+        "value_counts": "executed (site, vector, recursion step) updates",
         "config": {"workload": CONFIG_NAME, "sites": w.n_sites, "vacancies": len(w.vacancies),
                    "vectors_per_gpu": R, "moments": M, "dt_hbar_over_gamma0": DT, "bessel_terms": n_p,
                    "l2": "inputs larger than L2 (8 vector blocks x 134 MB)",
                    "parallelism": f"replicas x{world} (independent random vectors)"},
         "roofline": roofline,
-        "executed_site_updates_per_s": executed,
+        "paper_equivalent_site_updates_per_s": paper_value,
+        "paper_equivalent_note": "N R ((M - 1) + 4 (N_p - 1)) per correlation time, the recursion steps of "
+                                 "Algorithms 3, 5-7 as printed, over the same time",
         "gpu_launches": int(cnt["kpm_launches"] + cnt["evolve_launches"] + cnt["other_launches"]),
         "phase_ms": {"kpm": cnt["kpm_ms"], "evolve": cnt["evolve_ms"]},
         "clocks": clk,
-        "e2e": {"value": work / e2e_s, "unit": UNIT,
+        "e2e": {"value": executed_work / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(phi_host.numel() * 16 / K),
                 "d2h_bytes_per_step": int(out_host.numel() * 16 / K), "seconds": e2e_s},
         "sanity_bounded_moments": ok,
         "sigma": sigma,
     }
+    if c64 is not None:
+        line["c64"] = c64
     if world == 1 and not args.no_cpu_baseline and CONFIG_NAME == DEFAULT_WORKLOAD:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -437,6 +500,7 @@ def run_batched(args):
     phis = [torch.from_numpy(w.vectors(rv)).to("cuda") for w in ws]
     n_sites = sum(w.n_sites for w in ws)
     out = torch.zeros((len(ws), rv, mm), dtype=torch.complex128, device="cuda")
+    fp64_peak = fp64_peak_tflops(kg)
     for _ in range(args.warmup):
         kg.batched_dos_moments(hs, phis, mm, out=out)
     tune = kg.batched_tuning()
@@ -465,8 +529,9 @@ def run_batched(args):
     t0 = time.perf_counter()
     kg.batched_dos_moments(hs, phis_h, mm, out=out_h)
     e2e_s = time.perf_counter() - t0
-    work = float(n_sites) * rv * (mm - 1) * args.steps * world
-    steps_per_call = (mm + 1) // 2
+    steps_per_call = (mm + 1) // 2   # first step + (M - 1) / 2 doubling steps
+    work = float(n_sites) * rv * steps_per_call * args.steps * world
+    paper_work = float(n_sites) * rv * (mm - 1) * args.steps * world
     step_ms = ms / args.steps / steps_per_call
     # Anderson disorder adds the on-site term e x: one more DFMA per item (14 flops)
     flops = (KPM_FP64_FLOPS_PER_ITEM + 2) * n_sites * rv
@@ -482,20 +547,22 @@ def run_batched(args):
         "metric": METRIC, "value": work / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
+        "data": "synthetic", "value_counts": "executed (site, vector, recursion step) updates",
+        "paper_equivalent_site_updates_per_s": paper_work / (ms * 1e-3),
         "config": {"workload": BATCHED_WORKLOAD, "instances": len(ws), "sites": n_sites,
                    "vectors_per_instance": rv, "moments": mm,
                    "l2": "inputs larger than L2 (2 x 6.9 GB vector blocks)",
                    "parallelism": f"replicas x{world} (independent random vectors)"},
         "roofline": {"bound": "alu", "kernel": "batched_kpm_kernel<64,RB> (persistent FP64 doubling KPM)",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak, "traffic": None,
+                     "peak_source": "measured in-run (kg_fp64_fma_rate)",
                      "avg_step_ms": step_ms,
                      "hbm": {"achieved_gbs": bytes_step / (step_ms * 1e-3) / 1e9, "peak_gbs": hbm_peak}},
         "autotune": tune,
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
-        "e2e": {"value": float(n_sites) * rv * (mm - 1) / e2e_s, "unit": UNIT,
+        "e2e": {"value": float(n_sites) * rv * steps_per_call / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(p.numel() for p in phis_h) * 16),
                 "d2h_bytes_per_step": int(out_h.numel() * 16), "seconds": e2e_s},
         "sanity_bounded_moments": ok,
@@ -611,6 +678,8 @@ def run_small(args):
     def one_run(dst):
         kg.vac(h, phi, m, nc, dt, bessel_tol=TOL, out=dst)
 
+    fp64_peak = fp64_peak_tflops(kg)
+
     for _ in range(args.warmup):
         one_run(out)
     torch.cuda.synchronize()
@@ -641,8 +710,9 @@ def run_small(args):
     e2e_s = time.perf_counter() - t0
     # paper-counted work of one run: per time, M - 1 KPM steps; per time step, two chains
     # of N_p - 1 Chebyshev-Bessel terms (Algorithm 2)
-    work = float(w.n_sites) * (nc * (m - 1) + (nc - 1) * 2 * (n_p - 1))
+    paper_work = float(w.n_sites) * (nc * (m - 1) + (nc - 1) * 2 * (n_p - 1))
     per_run_s = ms * 1e-3 / args.steps
+    work = (cnt["kpm_site_steps"] + cnt["evolve_site_steps"]) / args.steps   # executed, per run
     # dominant kernel: the cluster KPM loop (vectors in shared memory, 6 DFMA = 12 FP64 flops per
     # site-vector step); its CUDA-event phase time covers the moment loops of the timed runs
     kpm_flop = 12.0 * cnt["kpm_site_steps"]
@@ -651,6 +721,8 @@ def run_small(args):
         "metric": METRIC, "value": work / per_run_s, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "value_counts": "executed (site, vector, recursion step) updates",
+        "paper_equivalent_site_updates_per_s": paper_work / per_run_s,
         "config": {"workload": SMALL_WORKLOAD, "sites": w.n_sites, "vacancies": len(w.vacancies),
                    "vectors": 1, "moments": m, "times": nc, "energies": 201, "bessel_terms": n_p,
                    "us_per_run": per_run_s * 1e6, "host_sums_us": sums_s * 1e6,
@@ -659,9 +731,9 @@ def run_small(args):
                          "one step = one whole run"},
         "roofline": {"bound": "alu", "kernel": "kpm_cluster_kernel<double,1> (VAC KPM steps, up to 256 per "
                                               "16-CTA cluster launch, vectors in shared memory)",
-                     "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                     "peak_source": "nominal FP64 of the profiling recipe (DFMA probe: 1.20)",
+                     "achieved": achieved_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / fp64_peak, "traffic": None,
+                     "peak_source": "measured in-run (kg_fp64_fma_rate)",
                      "note": "latency-bound: one recursion step over 4096 site-vectors takes about 1 us "
                              "(cluster barrier, distributed shared memory gathers, FP64 chain)"},
         "gpu_launches": int(cnt["kpm_launches"] + cnt["evolve_launches"] + cnt["other_launches"]),
@@ -675,7 +747,8 @@ def run_small(args):
         t0 = time.perf_counter()
         oracle.vac_moments(ho, w.vectors(1)[:, 0], m, nc, dt)
         sec = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": work / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+        # the oracle runs Algorithms 2, 5 and 6 as printed: its executed work is the paper count
+        line["cpu_baseline"] = {"value": paper_work / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"the whole run (VAC, 10 times, M = 512) in the oracle, one host "
                                           f"thread: {sec:.2f} s"}
     print(json.dumps(line), flush=True)

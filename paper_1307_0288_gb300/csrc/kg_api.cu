@@ -857,6 +857,39 @@ kg_status kg_timing_enable(kg_hamiltonian* h, int enable) {
     return KG_OK;
 }
 
+kg_status kg_fp64_fma_rate(int repeats, double* fma_per_s) {
+    clear_error();
+    if (!fma_per_s) return fail(KG_EINVAL, "fma_per_s is required");
+    if (repeats < 1 || repeats > 100) return fail(KG_EINVAL, "repeats must be in 1..100");
+    double* buf = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    auto cleanup = [&]() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        if (buf) cudaFree(buf);
+    };
+    const size_t bytes = (size_t)fp64_probe_grid() * 256 * sizeof(double);
+    cudaError_t e = cudaMalloc(&buf, bytes);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = launch_fp64_probe(buf, nullptr);   // warm-up
+    float best = 0.0f;
+    for (int k = 0; k < repeats && e == cudaSuccess; k++) {
+        e = cudaEventRecord(a, nullptr);
+        if (e == cudaSuccess) e = launch_fp64_probe(buf, nullptr);
+        if (e == cudaSuccess) e = cudaEventRecord(b, nullptr);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && ms > 0.0f && (best == 0.0f || ms < best)) best = ms;
+    }
+    cleanup();
+    if (e != cudaSuccess) return fail(KG_ECUDA, std::string("kg_fp64_fma_rate: ") + cudaGetErrorString(e));
+    if (best <= 0.0f) return fail(KG_ECUDA, "kg_fp64_fma_rate: no timed launch");
+    *fma_per_s = fp64_probe_fmas() / (best * 1e-3);
+    return KG_OK;
+}
+
 kg_status kg_timing_read(kg_hamiltonian* h, kg_timing* out) {
     if (!h || !out) return fail(KG_EINVAL, "NULL argument");
     KG_CUDA_TRY(cudaStreamSynchronize(h->stream));

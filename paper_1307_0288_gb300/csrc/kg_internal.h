@@ -186,4 +186,10 @@ int stream_grid(int64_t n_items);
 // NaN or infinite; one kernel launch on stream s.
 cudaError_t launch_nonfinite(const double* p, int64_t n, int* flag, cudaStream_t s);
 
+// FP64 FMA throughput probe: grid size (CTAs), FMA instructions per launch, and one
+// launch writing grid x 256 doubles to out.
+int fp64_probe_grid();
+double fp64_probe_fmas();
+cudaError_t launch_fp64_probe(double* out, cudaStream_t s);
+
 }  // namespace kg

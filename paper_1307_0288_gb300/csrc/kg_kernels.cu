@@ -145,6 +145,18 @@ __device__ __forceinline__ double2 mk<double>(double x, double y) { return make_
 template <>
 __device__ __forceinline__ float2 mk<float>(float x, float y) { return make_float2(x, y); }
 
+// Programmatic dependent launch.  The per-step kernels of a recursion are launched with
+// programmatic stream serialisation, so the CTAs of step n+1 may become resident while
+// step n still runs.  Each such kernel reads only constant data (the neighbour table,
+// the on-site energies) before pdl_wait(), which returns once the previous grid has
+// completed and its memory operations are visible; every read of a vector and every
+// write comes after it.  pdl_trigger() right after the wait lets the next step's CTAs
+// be scheduled as early as resources allow (they wait in turn), so the launch latency
+// and the CTA ramp of step n+1 overlap the tail of step n.  Launched without the
+// attribute, the wait returns at once and the trigger has no effect.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // --------------------------------------------------------------------------------
 // KPM step with phi_L = phi_R (DOS and MSD moments).  Uses the Chebyshev product
 // identity 2 T_m T_n = T_{m+n} + T_{|m-n|}, so one recursion step n yields two moments:
@@ -171,6 +183,8 @@ __global__ void __launch_bounds__(kBlock<T>) kpm_sym_kernel(DevH H, const vec2_t
     int64_t w = (int64_t)blockIdx.x * NT + threadIdx.x;
     Idx3 nid;
     if (w < n_items) nid = load_idx(H.idx, H.istride, w / R);
+    pdl_wait();
+    pdl_trigger();
     for (; w < n_items; w += stride) {
         const int64_t n = w / R;
         const Nbr<T> g = gather_at<T, R>(nid, n, r, cur);
@@ -211,6 +225,8 @@ __global__ void __launch_bounds__(kBlock<T>) kpm_gen_kernel(DevH H, const vec2_t
     int64_t w = (int64_t)blockIdx.x * NT + threadIdx.x;
     Idx3 nid;
     if (w < n_items) nid = load_idx(H.idx, H.istride, w / R);
+    pdl_wait();
+    pdl_trigger();
     for (; w < n_items; w += stride) {
         const int64_t n = w / R;
         const Nbr<T> g = gather_at<T, R>(nid, n, r, cur);
@@ -438,6 +454,8 @@ __global__ void __launch_bounds__(kThreads) kpm_sym_pair_kernel(DevH H, const fl
     int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     Idx3 nid;
     if (w < n_items) nid = load_idx(H.idx, H.istride, w / R2);
+    pdl_wait();
+    pdl_trigger();
     for (; w < n_items; w += stride) {
         const int64_t n = w / R2;
         const Nbr4 g = gather_pair<R2>(nid, n, r2, cur);
@@ -480,6 +498,8 @@ __global__ void __launch_bounds__(kThreads) kpm_gen_pair_kernel(DevH H, const fl
     int64_t w = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     Idx3 nid;
     if (w < n_items) nid = load_idx(H.idx, H.istride, w / R2);
+    pdl_wait();
+    pdl_trigger();
     for (; w < n_items; w += stride) {
         const int64_t n = w / R2;
         const Nbr4 g = gather_pair<R2>(nid, n, r2, cur);
@@ -625,6 +645,8 @@ __global__ void __launch_bounds__(kBlock<T>) evolve_kernel(DevH H, double j0d, d
     int64_t w = (int64_t)blockIdx.x * kBlock<T> + threadIdx.x;
     Idx3 nid;
     if (w < n_items) nid = load_idx(H.idx, H.istride, w / R);
+    pdl_wait();
+    pdl_trigger();
     for (; w < n_items; w += stride) {
         const int64_t n = w / R;
         const Idx3 id = nid;
@@ -821,6 +843,32 @@ static int one_wave_grid(K kernel, int64_t n_items, int threads = kThreads) {
     return (int)(g < 1 ? 1 : g);
 }
 
+// Launch with programmatic stream serialisation (see pdl_wait): used for the steps of a
+// recursion after the first, whose predecessor in the stream is the previous step (or a
+// reduction of partial sums), never a kernel that writes the neighbour table.
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Launch of a recursion step: the first step plainly, later steps with PDL.
+template <typename... KArgs, typename... Args>
+static void launch_step(bool first, void (*kernel)(KArgs...), int grid, int threads, cudaStream_t s,
+                        Args... args) {
+    if (first) kernel<<<grid, threads, 0, s>>>(args...);
+    else launch_pdl(kernel, grid, threads, s, args...);
+}
+
 #define KG_DISPATCH_R(R_, ...)                                   \
     switch (R_) {                                                \
         case 1: { constexpr int RR = 1; __VA_ARGS__; } break;    \
@@ -851,12 +899,12 @@ cudaError_t launch_kpm_sym(const DevH& H, int R, bool first, const vec2_t<T>* cu
             const float4* p4 = reinterpret_cast<const float4*>(prev);
             float4* o4 = reinterpret_cast<float4*>(out);
             KG_DISPATCH_R(R, if constexpr (RR >= 2) { KG_BOOL(ons, ON, KG_BOOL(first, FI,
-                kpm_sym_pair_kernel<RR, ON, FI><<<grid, kThreads, 0, s>>>(H, c4, p4, o4, partial))) });
+                launch_step(FI, kpm_sym_pair_kernel<RR, ON, FI>, grid, kThreads, s, H, c4, p4, o4, partial))) });
             return cudaGetLastError();
         }
     }
     KG_DISPATCH_R(R, KG_BOOL(ons, ON, KG_BOOL(first, FI,
-        kpm_sym_kernel<T, RR, ON, FI><<<grid, kBlock<T>, 0, s>>>(H, cur, prev, out, partial))));
+        launch_step(FI, kpm_sym_kernel<T, RR, ON, FI>, grid, kBlock<T>, s, H, cur, prev, out, partial))));
     return cudaGetLastError();
 }
 
@@ -872,12 +920,13 @@ cudaError_t launch_kpm_gen(const DevH& H, int R, bool first, const vec2_t<T>* L,
             const float4* p4 = reinterpret_cast<const float4*>(prev);
             float4* o4 = reinterpret_cast<float4*>(out);
             KG_DISPATCH_R(R, if constexpr (RR >= 2) { KG_BOOL(ons, ON, KG_BOOL(first, FI,
-                kpm_gen_pair_kernel<RR, ON, FI><<<grid, kThreads, 0, s>>>(H, l4, c4, p4, o4, partial))) });
+                launch_step(FI, kpm_gen_pair_kernel<RR, ON, FI>, grid, kThreads, s, H, l4, c4, p4, o4,
+                            partial))) });
             return cudaGetLastError();
         }
     }
     KG_DISPATCH_R(R, KG_BOOL(ons, ON, KG_BOOL(first, FI,
-        kpm_gen_kernel<T, RR, ON, FI><<<grid, kBlock<T>, 0, s>>>(H, L, cur, prev, out, partial))));
+        launch_step(FI, kpm_gen_kernel<T, RR, ON, FI>, grid, kBlock<T>, s, H, L, cur, prev, out, partial))));
     return cudaGetLastError();
 }
 
@@ -1070,7 +1119,7 @@ static void evolve_dispatch(const DevH& H, bool first, double j0, double cr, dou
     KG_BOOL(first, FI, KG_BOOL(ons, ON, KG_BOOL(ypar, YP, KG_BOOL(odd, OD,
         if constexpr (!FI || OD) {
             const int g = one_wave_grid(evolve_kernel<T, R, NCH, XC, FI, ON, YP, OD>, H.n * R, kBlock<T>);
-            evolve_kernel<T, R, NCH, XC, FI, ON, YP, OD><<<g, kBlock<T>, 0, s>>>(H, j0, cr, ci, ch);
+            launch_step(FI, evolve_kernel<T, R, NCH, XC, FI, ON, YP, OD>, g, kBlock<T>, s, H, j0, cr, ci, ch);
         }))));
 }
 
@@ -1155,6 +1204,42 @@ __global__ void nonfinite_kernel(const double* __restrict__ p, int64_t n, int* _
     bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) bad |= !isfinite(p[i]);
     if (__syncthreads_or(bad) && threadIdx.x == 0) *flag = 1;
+}
+
+// --------------------------------------------------------------------------------
+// FP64 FMA throughput probe: eight independent chains a <- a b + c per thread (the DP
+// pipe's latency is covered by the chains and the resident warps), one store per
+// thread so that nothing is dropped.  b and c arrive as arguments (no constant folding);
+// with b < 1 the chains converge to c / (1 - b) and stay normal.
+// --------------------------------------------------------------------------------
+constexpr int kFmaChains = 8;
+constexpr int kFmaIters = 2048;
+constexpr int kFmaThreads = 256;
+constexpr int kFmaCtasPerSm = 4;
+
+__global__ void __launch_bounds__(kFmaThreads) fp64_fma_probe_kernel(double b, double c, double* __restrict__ out) {
+    double a[kFmaChains];
+#pragma unroll
+    for (int k = 0; k < kFmaChains; k++) a[k] = (double)(threadIdx.x + k);
+    for (int i = 0; i < kFmaIters; i++) {
+#pragma unroll
+        for (int k = 0; k < kFmaChains; k++) a[k] = fma(a[k], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kFmaChains; k++) s += a[k];
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+int fp64_probe_grid() { return sm_count() * kFmaCtasPerSm; }
+
+double fp64_probe_fmas() {
+    return (double)fp64_probe_grid() * kFmaThreads * kFmaChains * kFmaIters;
+}
+
+cudaError_t launch_fp64_probe(double* out, cudaStream_t s) {
+    fp64_fma_probe_kernel<<<fp64_probe_grid(), kFmaThreads, 0, s>>>(0.9999999, 1e-3, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_nonfinite(const double* p, int64_t n, int* flag, cudaStream_t s) {
