@@ -40,26 +40,61 @@ def _blocks(n_vec: int, block: int):
 
 
 def einstein_curves(w, n_vec: int, n_moments: int, n_times: int, dt: float, energies_ev, *,
-                    block: int = 16, precision: int = KG_FP64):
+                    block: int = 16, precision: int = KG_FP64, per_vector: bool = False):
     """rho(E), rho DX^2(E, t_m) and the Einstein conductivities (Eqs. 9, 11) averaged over
-    n_vec random vectors, run in blocks of ``block`` vectors.  dt in hbar/gamma0."""
+    n_vec random vectors, run in blocks of ``block`` vectors.  dt in hbar/gamma0.  With
+    per_vector, also each vector's DOS and MSD moments (keys mu_dos_r, mu_msd_r)."""
     h = from_workload(w)
     phi = w.vectors(n_vec)
     mu_dos = np.zeros(n_moments)
     mu_msd = np.zeros((n_times, n_moments))
+    keep_dos, keep_msd = [], []
     t0 = time.perf_counter()
     for b0, b1 in _blocks(n_vec, block):
         ph = np.ascontiguousarray(phi[:, b0:b1])
-        mu_dos += dos_moments(h, ph, n_moments, precision=precision).real.sum(axis=0)
-        mu_msd += msd(h, ph, n_moments, n_times, dt, precision=precision).real.sum(axis=0)
+        d = dos_moments(h, ph, n_moments, precision=precision).real
+        m = msd(h, ph, n_moments, n_times, dt, precision=precision).real
+        mu_dos += d.sum(axis=0)
+        mu_msd += m.sum(axis=0)
+        if per_vector:
+            keep_dos.append(d)
+            keep_msd.append(m)
     seconds = time.perf_counter() - t0
     rho = kpm_sum(mu_dos / n_vec, energies_ev, h.emax_ev, h.area_nm2)
     rdx = kpm_sum(mu_msd / n_vec, energies_ev, h.emax_ev, h.area_nm2)
     t_fs = np.arange(n_times) * dt * HBAR_EV_FS / w.gamma0_ev
-    return {"t_fs": t_fs, "energies": np.asarray(energies_ev), "rho": rho, "rho_dx2": rdx,
-            "sigma_e1": conductivity(KG_SIGMA_E1, rdx, t_fs[1]),
-            "sigma_e2": conductivity(KG_SIGMA_E2, rdx, t_fs[1]),
-            "emax_ev": h.emax_ev, "area_nm2": h.area_nm2, "gpu_seconds": seconds}
+    out = {"t_fs": t_fs, "energies": np.asarray(energies_ev), "rho": rho, "rho_dx2": rdx,
+           "sigma_e1": conductivity(KG_SIGMA_E1, rdx, t_fs[1]),
+           "sigma_e2": conductivity(KG_SIGMA_E2, rdx, t_fs[1]),
+           "emax_ev": h.emax_ev, "area_nm2": h.area_nm2, "gpu_seconds": seconds}
+    if per_vector:
+        out["mu_dos_r"] = np.concatenate(keep_dos, axis=0)
+        out["mu_msd_r"] = np.concatenate(keep_msd, axis=0)
+    return out
+
+
+def jackknife_sigma_sc(c, t_block, plateau):
+    """Leave-one-vector-out (jackknife) estimates of the plateau means of sigma_sc by
+    maximum and by block average, from the per-vector moments of einstein_curves:
+    the stochastic trace (Sec. 3.1.1) averages independent random vectors, so the
+    spread of the leave-one-out estimates measures the statistical error of the
+    n-vector result.  Returns (mean_max, se_max, mean_avg, se_avg, n)."""
+    d, m = c["mu_dos_r"], c["mu_msd_r"]
+    n = d.shape[0]
+    sd, sm = d.sum(axis=0), m.sum(axis=0)
+    t = c["t_fs"]
+    est_max, est_avg = [], []
+    for i in range(n):
+        rdx = kpm_sum((sm - m[i]) / (n - 1), c["energies"], c["emax_ev"], c["area_nm2"])
+        s_max, s_avg = sigma_sc(conductivity(KG_SIGMA_E1, rdx, t[1]), t[1], *t_block)
+        est_max.append(s_max[plateau].mean())
+        est_avg.append(s_avg[plateau].mean())
+    est_max, est_avg = np.array(est_max), np.array(est_avg)
+
+    def se(v):
+        return float(np.sqrt((n - 1) / n * np.sum((v - v.mean()) ** 2)))
+
+    return float(est_max.mean()), se(est_max), float(est_avg.mean()), se(est_avg), n
 
 
 def green_kubo_curves(w, n_vec: int, n_moments: int, n_times: int, dt: float, energies_ev, *,
@@ -141,15 +176,23 @@ def run_diffusive(cells=(1024, 512), conc: float = 0.01, n_vec: int = 32, n_mome
     sigma^E1 on the same vectors (Green-Kubo = Einstein, Sec. 5.2)."""
     en = np.round(np.linspace(-1.0, 1.0, 81), 10)
     w = ki.sheet_cells(*cells, vacancy_conc=conc, n_vec=n_vec)
-    c = einstein_curves(w, n_vec, n_moments, n_times, dt, en, block=block)
+    c = einstein_curves(w, n_vec, n_moments, n_times, dt, en, block=block, per_vector=True)
     t = c["t_fs"]
     s_max, s_avg = sigma_sc(c["sigma_e1"], t[1], *t_block)
     plateau = (np.abs(en) >= 0.1 - 1e-9) & (np.abs(en) <= 0.25 + 1e-9)
+    jm, jse_max, ja, jse_avg, nj = jackknife_sigma_sc(c, t_block, plateau)
+    pm, pa = float(s_max[plateau].mean()), float(s_avg[plateau].mean())
     out = {"sites": w.n_sites, "vacancies": len(w.vacancies), "vectors": n_vec, "moments": n_moments,
            "dt_fs": float(t[1]), "t_max_fs": float(t[-1]), "t_block_fs": list(t_block),
            "energies_ev": en.tolist(), "sigma_sc_max": s_max.tolist(), "sigma_sc_average": s_avg.tolist(),
-           "plateau_mean_max": float(s_max[plateau].mean()),
-           "plateau_mean_average": float(s_avg[plateau].mean()),
+           "plateau_mean_max": pm, "plateau_mean_average": pa,
+           # jackknife over the n vectors: standard error of the n-vector plateau means, and the
+           # bias estimate (n - 1)(mean of leave-one-out - full) of each estimator
+           "plateau_se_max": jse_max, "plateau_se_average": jse_avg,
+           "plateau_jackknife_bias_max": (nj - 1) * (jm - pm),
+           "plateau_jackknife_bias_average": (nj - 1) * (ja - pa),
+           "plateau_max_minus_4_over_pi_in_se": (pm - 4.0 / np.pi) / jse_max if jse_max > 0 else None,
+           "plateau_average_minus_4_over_pi_in_se": (pa - 4.0 / np.pi) / jse_avg if jse_avg > 0 else None,
            "sigma_min_4_over_pi": 4.0 / np.pi, "gpu_seconds_einstein": c["gpu_seconds"]}
     if gk_vectors:
         wg = ki.sheet_cells(*cells, vacancy_conc=conc, n_vec=gk_vectors)

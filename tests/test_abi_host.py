@@ -209,3 +209,35 @@ def test_seeded_inputs_from_the_c_abi_match_the_input_module():
         assert np.max(np.abs(got - want)) <= ulp
         assert np.all(got[vac] == 0)
         print(f"{w.n_sites} sites: phase vectors bit-identical: {np.array_equal(got, want)}")
+
+
+def test_jackknife_error_of_sigma_sc_plateau():
+    """The jackknife over random vectors (regimes.jackknife_sigma_sc): identical vectors
+    give a zero error; for sigma_sc by block average, a linear function of the averaged
+    moments (Chebyshev sum, Eq. 31; central differences, Eq. 9; block average, Eq. 54),
+    the jackknife standard error equals the textbook standard error of the mean of the
+    single-vector estimates."""
+    from paper_1307_0288_gb300 import regimes
+    rng = np.random.default_rng(5)
+    n, nt, m = 7, 12, 64
+    en = np.linspace(-1.0, 1.0, 21)
+    base_d = np.zeros(m)
+    base_d[0] = 1000.0
+    base_m = np.outer(np.arange(nt) ** 2, np.exp(-np.arange(m) / 8.0)) * 50.0
+    c = {"t_fs": np.arange(nt) * 0.5, "energies": en, "emax_ev": 8.5, "area_nm2": 400.0,
+         "mu_dos_r": np.tile(base_d, (n, 1)), "mu_msd_r": np.tile(base_m, (n, 1, 1))}
+    plateau = np.abs(en) <= 0.3
+    jm, se_max, ja, se_avg, nj = regimes.jackknife_sigma_sc(c, (1.0, 4.0), plateau)
+    assert nj == n and se_max <= 1e-12 * abs(jm) and se_avg <= 1e-12 * abs(ja)   # rounding only
+    c["mu_msd_r"] = base_m[None] * (1.0 + 0.2 * rng.standard_normal((n, 1, 1))) + \
+        rng.standard_normal((n, nt, m)) * 5.0
+    jm, se_max, ja, se_avg, _ = regimes.jackknife_sigma_sc(c, (1.0, 4.0), plateau)
+    single = []
+    for i in range(n):
+        rdx = kg.kpm_sum(c["mu_msd_r"][i], en, 8.5, 400.0)
+        s = kg.conductivity(kg.KG_SIGMA_E1, rdx, 0.5)
+        single.append(kg.sigma_sc(s, 0.5, 1.0, 4.0)[1][plateau].mean())
+    single = np.array(single)
+    assert se_avg > 0
+    assert abs(se_avg - single.std(ddof=1) / np.sqrt(n)) < 1e-9 * max(1.0, se_avg)
+    assert abs(ja - single.mean()) < 1e-9 * max(1.0, abs(ja))
