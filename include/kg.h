@@ -269,15 +269,17 @@ kg_status kg_batched_release(void);
  * allocation failures on the host; the handle stays usable once the cap is lifted. */
 kg_status kg_test_alloc_cap(uint64_t bytes);
 
-/* Execution option for small instances (Algorithm 5's recursion loop; no new arithmetic).
- * When one recursion step of a moment loop needs at most 16 CTAs (up to 8192 site-vectors,
- * R <= 16), a launch per step costs more than the step, so by default (enable = 1) up to
- * 256 steps run in one launch of a single thread-block cluster that keeps the vectors in
- * its shared memory and separates the steps with the cluster's hardware barrier.  The
- * Chebyshev vectors are bitwise those of one launch per step; the moments' inner
- * products are summed in another order (double-float sums; the two paths agree within
- * 1e-12 of the largest moment).  enable = 0 selects one launch per step for every size.
- * Process-wide; takes effect on the next call. */
+/* Execution option for small instances (the recursion loops of Algorithms 5-7; no new
+ * arithmetic).  When one recursion step needs at most 16 CTAs (up to 8192 site-vectors,
+ * R <= 16), a launch per step costs more than the step, so by default (enable = 1) the
+ * steps run in launches of a single thread-block cluster that keeps the vectors in its
+ * shared memory and separates the steps with the cluster's hardware barrier: up to 256
+ * moment steps per launch, and the whole Chebyshev-Bessel series of a time step (up to
+ * 96 terms, all chains) in one launch.  The Chebyshev vectors and the propagated vectors
+ * are bitwise those of one launch per step; the moments' inner products are summed in
+ * another order (double-float sums; the two paths agree within 1e-12 of the largest
+ * moment).  enable = 0 selects one launch per step for every size.  Process-wide; takes
+ * effect on the next call. */
 kg_status kg_set_small_persistent(int enable);
 
 /* Test hook for failure detection: CTA `cta` of the cached batch stops publishing its

@@ -312,6 +312,27 @@ static kg_status run_series(kg_hamiltonian* h, int R, const Series& ser, int s, 
     using V2 = vec2_t<T>;
     PhaseTimer t(h, 1);
     ChainsT<T> ch;
+    const int nterms = std::max(ser.np - 1, 1);   // the m = 1 term runs even when N_p = 1 (with c_1 = 0)
+    ClusterPlan plan;
+    if (g_small_persistent.load() && nterms <= kClusterMaxTerms &&
+        evolve_cluster_plan<T>(h->dev, R, nch, xc, &plan)) {
+        // small instance: the whole series in one cluster launch, chains in shared memory;
+        // the inputs are left unchanged
+        SeriesCoef cf;
+        cf.j0 = ser.j[0];
+        cf.nterms = nterms;
+        for (int m = 1; m <= nterms; m++)
+            if (m < ser.np) term_coef(ser, m, s, &cf.cr[m], &cf.ci[m]);
+        for (int k = 0; k < nch; k++) {
+            ch.cur[k] = in[k];
+            ch.acc[k] = acc[k];
+        }
+        if (xc) ch.qacc = qacc;
+        KG_CUDA_TRY(launch_evolve_cluster<T>(h->dev, R, nch, xc, plan, cf, ch, h->stream));
+        h->counters.evolve_launches += 1;
+        h->counters.evolve_site_steps += (double)h->n * R * (nch + (xc ? 1 : 0)) * nterms;
+        return KG_OK;
+    }
     V2* cur[3];
     V2* prv[3];
     for (int k = 0; k < nch; k++) {

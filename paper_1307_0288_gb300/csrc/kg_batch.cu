@@ -169,13 +169,20 @@ __global__ void __launch_bounds__(kBThreads) batched_kpm_kernel(BatchArgs a) {
 #pragma unroll
             for (int q = 0; q < kChunks; q++) {
                 const int r = q * RB + rl;
-                // vectors are rewritten by other CTAs during the kernel: L2-coherent loads
-                const double2 va = __ldcg(cur + (int64_t)i0 * R + r);
-                const double2 vb = __ldcg(cur + (int64_t)i1 * R + r);
-                const double2 vc = __ldcg(cur + (int64_t)i2 * R + r);
-                const double2 x = __ldcg(cur + site * R + r);
+                // Vectors are rewritten by other CTAs during the kernel, so no read-only
+                // (non-coherent) loads.  Plain cached loads are coherent here: every value read
+                // in step n was written before a release (st.release.gpu of the writer's step
+                // flag) that this CTA's ld.acquire.gpu observed before the barrier above, so by
+                // the PTX memory model these weak loads cannot return older values (the
+                // acquire invalidates the SM's L1), and nothing read in step n is rewritten
+                // before this CTA publishes step n.  L1 then serves the in-chain neighbours
+                // (adjacent rows) as in the per-step kernels.
+                const double2 va = __ldca(cur + (int64_t)i0 * R + r);
+                const double2 vb = __ldca(cur + (int64_t)i1 * R + r);
+                const double2 vc = __ldca(cur + (int64_t)i2 * R + r);
+                const double2 x = __ldca(cur + site * R + r);
                 double2 z = make_double2(0.0, 0.0);
-                if (n > 0) z = __ldcg(out + site * R + r);
+                if (n > 0) z = __ldca(out + site * R + r);
                 const double tr = ONSITE ? fma(e, x.x, -z.x) : -z.x;
                 const double ti = ONSITE ? fma(e, x.y, -z.y) : -z.y;
                 const double yr = fma(c, va.x, fma(c, vb.x, fma(c, vc.x, tr)));

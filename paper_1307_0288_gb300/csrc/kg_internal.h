@@ -158,6 +158,28 @@ struct ChainsT {
     V2* qacc = nullptr;             // null: accumulate into acc[0]
 };
 
+// Small instances: a whole Chebyshev-Bessel series (terms m = 1 .. nterms) in one
+// cluster launch.  cr[m], ci[m] are the coefficients 2 J_m (s i)^m of term m (index 0
+// unused); j0 = J_0.  Series longer than kClusterMaxTerms take the per-term launches.
+constexpr int kClusterMaxTerms = 96;
+struct SeriesCoef {
+    double j0 = 0.0;
+    double cr[kClusterMaxTerms + 1] = {0};
+    double ci[kClusterMaxTerms + 1] = {0};
+    int nterms = 0;
+};
+
+// Chooses the cluster plan of the series kernel for this H, R, nch and xc (cached per
+// device); false when the instance is too large or no such cluster fits.
+template <typename T>
+bool evolve_cluster_plan(const DevH& H, int R, int nch, bool xc, ClusterPlan* plan);
+
+// The series on the chains ch.cur[k] (inputs, not modified) into ch.acc[k] (and the
+// commutator chain into ch.qacc, or into ch.acc[0] when null), in one cluster launch.
+template <typename T>
+cudaError_t launch_evolve_cluster(const DevH& H, int R, int nch, bool xc, const ClusterPlan& plan,
+                                  const SeriesCoef& cf, const ChainsT<T>& ch, cudaStream_t s);
+
 // One term m of the Chebyshev-Bessel series on nch plain chains (+ the commutator
 // chain when xc).  first = the m = 1 step (also adds the J_0 term).  The grid is one
 // resident wave of the selected kernel.

@@ -138,6 +138,19 @@ __device__ __forceinline__ T hop(T c, T a, T b, T c3, T e, T x, T z, bool onsite
     return fma(c, a, fma(c, b, fma(c, c3, t)));
 }
 
+// (s i)^m is real for even m and imaginary for odd m, so ODD selects the two FMAs that
+// the non-zero part of the coefficient needs: acc += cr * y  or  acc += i ci * y.
+template <typename T>
+__device__ __forceinline__ void add_term(vec2_t<T>& a, bool odd, T cr, T ci, T yr, T yi) {
+    if (odd) {
+        a.x = fma(-ci, yi, a.x);
+        a.y = fma(ci, yr, a.y);
+    } else {
+        a.x = fma(cr, yr, a.x);
+        a.y = fma(cr, yi, a.y);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ vec2_t<T> mk(T x, T y);
 template <>
@@ -422,6 +435,171 @@ __global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T
 }
 
 // --------------------------------------------------------------------------------
+// Small instances: the whole Chebyshev-Bessel series of one time step (Algorithms 6
+// and 7, Eqs. 36-39) in one launch of one thread-block cluster.
+// Per term the per-term kernel below (evolve_kernel) is a few microseconds of launch
+// for a few microseconds of work; here the cluster's CTAs keep, for every chain, the two
+// latest terms p_{m-1} and p_{m-2} in shared memory (two buffers of nt + 1 entries per
+// chain, entry nt a permanent zero), read the neighbours of p_{m-1} through distributed
+// shared memory, write p_m in place over p_{m-2}, and keep the series accumulators in
+// registers.  The commutator chain q_m of the last plain chain (Eq. 39) is a third
+// chain with its own two buffers.  One cluster barrier separates the terms.  The
+// arithmetic of a term (hop, add_term and their order) is that of evolve_kernel, so the
+// results are bitwise those of the per-term launches.
+// --------------------------------------------------------------------------------
+template <typename T, int R, int NCH, bool XC, bool ONSITE, bool YPAR>
+__global__ void __launch_bounds__(512) evolve_cluster_kernel(DevH H, ChainsT<T> ch, SeriesCoef cf, int log_nt) {
+    static_assert(R <= kClusterMaxR, "cluster path: at most 16 vectors per block");
+    using V2 = vec2_t<T>;
+    constexpr int NB = NCH + (XC ? 1 : 0);   // chains held in shared memory
+    extern __shared__ __align__(16) unsigned char kg_cluster_smem[];
+    const int nt = 1 << log_nt;
+    V2* sv = reinterpret_cast<V2*>(kg_cluster_smem);   // [NB][2][nt + 1]
+    const int t = threadIdx.x;
+    const int r = t & (R - 1);
+    const int64_t n_items = H.n * R;
+    const int64_t w = ((int64_t)blockIdx.x << log_nt) + t;
+    const bool valid = w < n_items;
+    const V2 zero = mk<T>(0, 0);
+    auto buf = [&](int k, int b) { return sv + (k * 2 + b) * (nt + 1); };
+
+#pragma unroll
+    for (int k = 0; k < NCH; k++) {
+        buf(k, 0)[t] = valid ? ch.cur[k][w] : zero;
+        buf(k, 1)[t] = zero;
+    }
+    if constexpr (XC) {
+        buf(NCH, 0)[t] = zero;
+        buf(NCH, 1)[t] = zero;
+    }
+    if (t == 0) {
+        for (int k = 0; k < NB; k++) {
+            buf(k, 0)[nt] = zero;
+            buf(k, 1)[nt] = zero;
+        }
+    }
+    // cluster addresses of the three neighbours in buffer (0, 0); buffer (k, b) is
+    // (2 k + b)(nt + 1) entries further on
+    const int64_t n = valid ? w / R : H.n;
+    uint32_t na[3];
+    {
+        const Idx3 j = valid ? load_idx(H.idx, H.istride, n) : Idx3{(int32_t)H.n, (int32_t)H.n, (int32_t)H.n};
+        const int32_t jj[3] = {j.i0, j.i1, j.i2};
+        const uint32_t base = (uint32_t)__cvta_generic_to_shared(sv);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const int64_t item = (int64_t)jj[q] * R + r;
+            const bool zr = jj[q] >= H.n;
+            const uint32_t rank = zr ? blockIdx.x : (uint32_t)(item >> log_nt);
+            const uint32_t slot = zr ? (uint32_t)nt : (uint32_t)(item & (nt - 1));
+            na[q] = map_cluster_rank(base + slot * (uint32_t)sizeof(V2), rank);
+        }
+    }
+    T e1 = 0, e2 = 0;
+    if constexpr (ONSITE) {
+        const double o = valid ? __ldg(H.onsite + n) : 0.0;
+        e1 = (T)(1.0 * o);
+        e2 = (T)(2.0 * o);
+    }
+    double d0d = 0, d1d = 0, d2d = 0;
+    if constexpr (XC) {
+        if constexpr (YPAR) {
+            const int p = valid ? __ldg(H.parity + n) : 0;
+            d0d = H.dh[p][0]; d1d = H.dh[p][1]; d2d = H.dh[p][2];
+        } else {
+            d0d = H.dh[0][0]; d1d = H.dh[0][1]; d2d = H.dh[0][2];
+        }
+    }
+    const bool q_into_0 = (ch.qacc == nullptr);
+    const T j0 = (T)cf.j0;
+    const uint32_t bstride = (uint32_t)((nt + 1) * sizeof(V2));
+    V2 acc[NCH];
+    V2 qa = zero;
+    cluster_barrier();   // every CTA's buffers are filled before any peer reads them
+
+    int cb = 0;   // buffer holding p_{m-1}
+    for (int m = 1; m <= cf.nterms; m++) {
+        const bool first = m == 1;
+        const T c = first ? (T)H.h : (T)(2.0 * H.h);
+        const T e = first ? e1 : e2;
+        const T cr = (T)cf.cr[m], ci = (T)cf.ci[m];
+        const bool odd = first || cf.cr[m] == 0.0;
+        V2 q_add = zero;
+        V2 gsa = zero, gsb = zero, gsc = zero;
+#pragma unroll
+        for (int k = 0; k < NCH; k++) {
+            const uint32_t off = (uint32_t)(k * 2 + cb) * bstride;
+            V2 ga, gb, gc;
+            ld_cluster(na[0] + off, ga);
+            ld_cluster(na[1] + off, gb);
+            ld_cluster(na[2] + off, gc);
+            const V2 x = buf(k, cb)[t];
+            const V2 z = first ? zero : buf(k, cb ^ 1)[t];
+            const T yr = hop<T>(c, ga.x, gb.x, gc.x, e, x.x, z.x, ONSITE);
+            const T yi = hop<T>(c, ga.y, gb.y, gc.y, e, x.y, z.y, ONSITE);
+            if (valid) buf(k, cb ^ 1)[t] = mk<T>(yr, yi);
+            V2 a = first ? mk<T>(j0 * x.x, j0 * x.y) : acc[k];
+            add_term<T>(a, odd, cr, ci, yr, yi);
+            if (k == 0) q_add = a;
+            else acc[k] = a;
+            if (k == NCH - 1) {
+                gsa = ga;
+                gsb = gb;
+                gsc = gc;
+            }
+        }
+        if constexpr (XC) {
+            const T cx = first ? (T)1 : (T)2;
+            const T d0 = cx * (T)d0d, d1 = cx * (T)d1d, d2 = cx * (T)d2d;
+            T qr, qi;
+            if (first) {
+                if constexpr (YPAR) {
+                    qr = fma(d0, gsa.x, fma(d1, gsb.x, d2 * gsc.x));
+                    qi = fma(d0, gsa.y, fma(d1, gsb.y, d2 * gsc.y));
+                } else {
+                    qr = fma(d0, gsa.x, d1 * gsb.x);
+                    qi = fma(d0, gsa.y, d1 * gsb.y);
+                }
+            } else {
+                const uint32_t off = (uint32_t)(NCH * 2 + cb) * bstride;
+                V2 qa0, qb0, qc0;
+                ld_cluster(na[0] + off, qa0);
+                ld_cluster(na[1] + off, qb0);
+                ld_cluster(na[2] + off, qc0);
+                const V2 qx = buf(NCH, cb)[t];
+                const V2 qz = buf(NCH, cb ^ 1)[t];   // zero at m = 2 (q_0 = 0)
+                qr = hop<T>(c, qa0.x, qb0.x, qc0.x, e, qx.x, qz.x, ONSITE);
+                qi = hop<T>(c, qa0.y, qb0.y, qc0.y, e, qx.y, qz.y, ONSITE);
+                if constexpr (YPAR) {
+                    qr = fma(d0, gsa.x, fma(d1, gsb.x, fma(d2, gsc.x, qr)));
+                    qi = fma(d0, gsa.y, fma(d1, gsb.y, fma(d2, gsc.y, qi)));
+                } else {
+                    qr = fma(d0, gsa.x, fma(d1, gsb.x, qr));
+                    qi = fma(d0, gsa.y, fma(d1, gsb.y, qi));
+                }
+            }
+            if (valid) buf(NCH, cb ^ 1)[t] = mk<T>(qr, qi);
+            if (q_into_0) {
+                add_term<T>(q_add, odd, cr, ci, qr, qi);
+            } else {
+                if (first) qa = zero;
+                add_term<T>(qa, odd, cr, ci, qr, qi);
+            }
+        }
+        acc[0] = q_add;
+        cluster_barrier();
+        cb ^= 1;
+    }
+    if (valid) {
+#pragma unroll
+        for (int k = 0; k < NCH; k++) ch.acc[k][w] = acc[k];
+        if constexpr (XC) {
+            if (!q_into_0) ch.qacc[w] = qa;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------------
 // complex64 KPM steps with 128-bit accesses: for R >= 2 one thread owns the two adjacent
 // vectors (2 r2, 2 r2 + 1) of a site and moves them as one float4, halving the load and
 // store instructions per byte of the HBM-bound FP32 step.  Per-vector partial sums are
@@ -618,18 +796,6 @@ __global__ void reduce_ring_kernel(const double* __restrict__ ring, int slab0, i
 // [X,H~] has the same sparsity as H~ with per-slot factors (X_n - X_m) H~_nm, so it
 // reuses the gathered neighbours of chain s.
 // --------------------------------------------------------------------------------
-// (s i)^m is real for even m and imaginary for odd m, so ODD selects the two FMAs that
-// the non-zero part of the coefficient needs: acc += cr * y  or  acc += i ci * y.
-template <typename T>
-__device__ __forceinline__ void add_term(vec2_t<T>& a, bool odd, T cr, T ci, T yr, T yi) {
-    if (odd) {
-        a.x = fma(-ci, yi, a.x);
-        a.y = fma(ci, yr, a.y);
-    } else {
-        a.x = fma(cr, yr, a.x);
-        a.y = fma(cr, yi, a.y);
-    }
-}
 
 template <typename T, int R, int NCH, bool XC, bool FIRST, bool ONSITE, bool YPAR, bool ODD>
 __global__ void __launch_bounds__(kBlock<T>) evolve_kernel(DevH H, double j0d, double crd, double cid,
@@ -1048,6 +1214,81 @@ cudaError_t launch_kpm_cluster(const DevH& H, int R, bool sym, const ClusterPlan
 }
 
 template <typename T>
+static cudaError_t evolve_cluster_dispatch(const DevH& H, int R, int nch, bool xc, const ClusterPlan& p,
+                                           bool query, const SeriesCoef& cf, const ChainsT<T>& ch,
+                                           cudaStream_t s) {
+    const bool ons = H.onsite != nullptr, ypar = H.ytransport;
+    cudaError_t e = cudaErrorNotSupported;
+    const int nt = 1 << p.log_nt;
+    KG_DISPATCH_R16(R, KG_BOOL(ons, ON, KG_BOOL(ypar, YP,
+        if (nch == 1 && !xc) e = launch_single_cluster(evolve_cluster_kernel<T, RR, 1, false, ON, YP>, p.grid, nt,
+                                                       p.smem, query, s, H, ch, cf, p.log_nt);
+        else if (nch == 1) e = launch_single_cluster(evolve_cluster_kernel<T, RR, 1, true, ON, YP>, p.grid, nt,
+                                                     p.smem, query, s, H, ch, cf, p.log_nt);
+        else if (!xc) e = launch_single_cluster(evolve_cluster_kernel<T, RR, 2, false, ON, YP>, p.grid, nt,
+                                                p.smem, query, s, H, ch, cf, p.log_nt);
+        else e = launch_single_cluster(evolve_cluster_kernel<T, RR, 2, true, ON, YP>, p.grid, nt, p.smem,
+                                       query, s, H, ch, cf, p.log_nt))));
+    return e;
+}
+
+template <typename T>
+bool evolve_cluster_plan(const DevH& H, int R, int nch, bool xc, ClusterPlan* plan) {
+    if (R < 1 || R > kClusterMaxR || (R & (R - 1)) || nch < 1 || nch > 2) return false;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    struct Key {
+        int dev, tsize, R, nch, xc, ons, ypar;
+        int64_t n;
+        bool operator==(const Key& o) const {
+            return dev == o.dev && tsize == o.tsize && R == o.R && nch == o.nch && xc == o.xc && ons == o.ons &&
+                   ypar == o.ypar && n == o.n;
+        }
+    };
+    struct KeyHash {
+        size_t operator()(const Key& k) const {
+            return std::hash<int64_t>()(k.n) ^ ((size_t)k.dev << 48) ^ ((size_t)k.tsize << 40) ^
+                   ((size_t)k.R << 32) ^ ((size_t)k.nch << 28) ^ ((size_t)k.xc << 27) ^ ((size_t)k.ons << 26) ^
+                   ((size_t)k.ypar << 25);
+        }
+    };
+    static thread_local std::unordered_map<Key, ClusterPlan, KeyHash> cache;
+    const Key k{dev, (int)sizeof(T), R, nch, xc ? 1 : 0, H.onsite ? 1 : 0, H.ytransport ? 1 : 0, H.n};
+    auto it = cache.find(k);
+    if (it == cache.end()) {
+        ClusterPlan best;
+        const int64_t items = H.n * R;
+        const int nb = nch + (xc ? 1 : 0);
+        for (int log_nt = 7; log_nt <= 9 && best.grid == 0; log_nt++) {
+            const int64_t nt = (int64_t)1 << log_nt;
+            const int64_t grid = (items + nt - 1) / nt;
+            if (grid < 1 || grid > kMaxCluster) continue;
+            const size_t smem = (size_t)nb * 2 * (size_t)(nt + 1) * sizeof(vec2_t<T>);
+            if (smem > kClusterSmemBudget) continue;
+            ClusterPlan p;
+            p.log_nt = log_nt;
+            p.grid = (int)grid;
+            p.chunk = kClusterMaxTerms;
+            p.smem = smem;
+            SeriesCoef none;
+            const cudaError_t e = evolve_cluster_dispatch<T>(H, R, nch, xc, p, true, none, ChainsT<T>{}, nullptr);
+            if (e != cudaSuccess) cudaGetLastError();   // a refused query must not leak into later launch checks
+            else best = p;
+        }
+        it = cache.emplace(k, best).first;
+    }
+    *plan = it->second;
+    return plan->grid > 0;
+}
+
+template <typename T>
+cudaError_t launch_evolve_cluster(const DevH& H, int R, int nch, bool xc, const ClusterPlan& p,
+                                  const SeriesCoef& cf, const ChainsT<T>& ch, cudaStream_t s) {
+    if (cf.nterms < 1 || cf.nterms > kClusterMaxTerms || p.grid < 1) return cudaErrorInvalidValue;
+    return evolve_cluster_dispatch<T>(H, R, nch, xc, p, false, cf, ch, s);
+}
+
+template <typename T>
 int kpm_grid(const DevH& H, int R, bool sym) {
     const bool ons = H.onsite != nullptr;
     if constexpr (kPaired<T>) {
@@ -1186,6 +1427,9 @@ cudaError_t launch_to_c64(const double2* in, float2* out, int64_t n_items, cudaS
     template cudaError_t launch_kpm_cluster<T>(const DevH&, int, bool, const ClusterPlan&,         \
                                                const vec2_t<T>*, const vec2_t<T>*, const vec2_t<T>*, \
                                                vec2_t<T>*, double*, int, cudaStream_t);             \
+    template bool evolve_cluster_plan<T>(const DevH&, int, int, bool, ClusterPlan*);                \
+    template cudaError_t launch_evolve_cluster<T>(const DevH&, int, int, bool, const ClusterPlan&,   \
+                                                  const SeriesCoef&, const ChainsT<T>&, cudaStream_t); \
     template cudaError_t launch_evolve<T>(const DevH&, int, int, bool, bool, double, double, double, \
                                           const ChainsT<T>&, cudaStream_t);                        \
     template cudaError_t launch_apply<T>(const DevH&, int, int, double, const vec2_t<T>*,           \

@@ -126,11 +126,24 @@ __device__ __forceinline__ uint64_t gelu2(uint64_t z) {
     const float2 uu = f2_unpack(u);
     return f2_fma(hz, f2_pack(tanh_hw(uu.x), tanh_hw(uu.y)), hz);
 }
-// BF16 pair (low = first) of GELU(z0), GELU(z1).
+// BF16 pair (low = first) of GELU(z0), GELU(z1), for activations that are stored as
+// BF16 anyway (the next layer's tensor-core operand).  The argument u of tanh is formed
+// in FP32 as in gelu2(); then u and z/2 are rounded to BF16 pairs, tanh runs as one
+// packed BF16 SFU instruction for both values (tanh.approx.bf16x2: half the SFU work of
+// two FP32 tanh), and z/2 (1 + tanh u) is one packed BF16 FMA whose single rounding
+// gives the stored pair.  Error: a few BF16 units in the last place of the result
+// (against half a unit when every step before the final rounding is FP32).
 __device__ __forceinline__ uint32_t gelu2_bf16(float z0, float z1) {
-    const float2 g = f2_unpack(gelu2(f2_pack(z0, z1)));
-    const __nv_bfloat162 b2 = __floats2bfloat162_rn(g.x, g.y);
-    return *(const uint32_t*)&b2;
+    const uint64_t z = f2_pack(z0, z1);
+    const uint64_t kc = f2_pack(kGeluK * kGeluC, kGeluK * kGeluC), k = f2_pack(kGeluK, kGeluK);
+    const float2 u = f2_unpack(f2_mul(z, f2_fma(kc, f2_mul(z, z), k)));
+    const float2 hz = f2_unpack(f2_mul(f2_pack(0.5f, 0.5f), z));
+    uint32_t ub, hb, tb, r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(ub) : "f"(u.y), "f"(u.x));     // high half = second value
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(tb) : "r"(ub));
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hb) : "f"(hz.y), "f"(hz.x));
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(hb), "r"(tb), "r"(hb));
+    return r;
 }
 
 __device__ __forceinline__ float gelu_grad(float z) {
@@ -623,9 +636,8 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                             z = f2_fma(f2_pack(w[3 * e + 2], w[3 * e + 5]), f2_pack(xr[i][2], xr[i][2]), z);
                             z = f2_fma(f2_pack(w[3 * e + 1], w[3 * e + 4]), f2_pack(xr[i][1], xr[i][1]), z);
                             z = f2_fma(f2_pack(w[3 * e], w[3 * e + 3]), f2_pack(xr[i][0], xr[i][0]), z);
-                            const float2 g = f2_unpack(gelu2(z));
-                            const __nv_bfloat162 b2 = __floats2bfloat162_rn(g.x, g.y);
-                            packed[e >> 1] = *(const uint32_t*)&b2;
+                            const float2 zz = f2_unpack(z);
+                            packed[e >> 1] = gelu2_bf16(zz.x, zz.y);
                         }
                         st_shared_v4(sA + t * kFTile + (uint32_t)((ch * BM + lane + 32 * i) * 16),
                                      make_uint4(packed[0], packed[1], packed[2], packed[3]));

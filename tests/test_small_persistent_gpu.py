@@ -128,3 +128,81 @@ def test_complex64(r):
     assert _rel(a, b) < 1e-9
     a, b = _both(lambda: kg.vac(h, phi, 300, 2, 1.0, precision=kg.KG_C64))
     assert _rel(a.reshape(r, -1), b.reshape(r, -1)) < 1e-9
+
+
+# ------------------------------------------------------------------ evolution series
+
+def _evolve_both(h, dt, which, x):
+    out = torch.empty_like(x)
+
+    def run():
+        kg.evolve(h, dt, which, x, out)
+        return out.clone()
+
+    return _both(run)
+
+
+@pytest.mark.parametrize("r", [1, 4])
+def test_evolve_series_cluster_is_bitwise_the_per_term_path(r):
+    """The Chebyshev-Bessel series of U(+dt), U(-dt) and [X, U(dt)] (Algorithms 6-7) in one
+    cluster launch equals the per-term launches bit for bit (same arithmetic, no
+    reductions), on every lattice kind (transport along y uses the parity-dependent
+    commutator factors), with vacancies and Anderson disorder, and against the oracle."""
+    for w in [ki.sheet_cells(12, 9, vacancy_conc=0.03, anderson_w_ev=1.1, lattice_seed=35),
+              ki.zgnr(10, 30, vacancy_conc=0.01, lattice_seed=36),
+              ki.Workload(ki.AGNR, 11, 40, vacancy_conc=0.02, anderson_w_ev=0.6, lattice_seed=37),
+              ki.Workload(ki.SHEET_OPEN_X, 14, 12, vacancy_conc=0.02, lattice_seed=38)]:
+        h = kg.from_workload(w)
+        ho = oracle.from_workload(w)
+        phi = w.vectors(r)
+        x = torch.from_numpy(np.ascontiguousarray(phi)).to("cuda")
+        for dt in (0.41, 2.0, 9.0):
+            tau = oracle.tau_of(ho, dt)
+            for which, ref in [(kg.KG_U_FORWARD, lambda v: oracle.evolve(ho, v, tau, +1)),
+                               (kg.KG_U_BACKWARD, lambda v: oracle.evolve(ho, v, tau, -1)),
+                               (kg.KG_U_COMMUTATOR, lambda v: oracle.evolvex(ho, v, tau))]:
+                a, b = _evolve_both(h, dt, which, x)
+                assert torch.equal(a, b), (w.kind, dt, which)
+                got = a.cpu().numpy()
+                want = np.stack([ref(phi[:, k]) for k in range(r)], axis=1)
+                assert np.max(np.abs(got - want)) / np.max(np.abs(want)) < 1e-12, (w.kind, dt, which)
+
+
+def test_evolve_series_long_series_falls_back_to_per_term():
+    """A series longer than one cluster launch takes (dt = 40 hbar/gamma0, N_p above 96):
+    the per-term launches, still equal to the oracle."""
+    w = ki.sheet_cells(8, 8, vacancy_conc=0.02, lattice_seed=39)
+    h = kg.from_workload(w)
+    ho = oracle.from_workload(w)
+    phi = w.vectors(1)
+    x = torch.from_numpy(np.ascontiguousarray(phi)).to("cuda")
+    assert len(kg.bessel_series(h.emax_ev * 40.0 / w.gamma0_ev, 1e-15)) > 97
+    out = torch.empty_like(x)
+    kg.timing_enable(h, True)
+    kg.evolve(h, 40.0, kg.KG_U_FORWARD, x, out)
+    n = kg.timing_read(h)["evolve_launches"]
+    kg.timing_enable(h, False)
+    assert n > 90
+    want = oracle.evolve(ho, phi[:, 0], oracle.tau_of(ho, 40.0), +1)
+    assert np.max(np.abs(out.cpu().numpy()[:, 0] - want)) / np.max(np.abs(want)) < 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [(kg.KG_FP64, 0.0), (kg.KG_C64, 1e-9)])
+def test_vac_and_msd_time_loops_one_series_launch_per_time_step(precision, tol):
+    """VAC (two chains U(-dt)A, U(-dt)B) and MSD (U(dt)xi, U(dt)psi and the commutator
+    chain) on the 4096-site sheet: one evolution launch per time step, and the moments of
+    the cluster path equal to the per-step path (FP64: the propagated vectors are bitwise
+    equal, the moments then differ only by the cluster KPM's summation order)."""
+    w = ki.sheet_cells(32, 32, vacancy_conc=0.01)
+    h = kg.from_workload(w)
+    phi = w.vectors(1)
+    nc = 6
+    for fn in (kg.vac, kg.msd):
+        kg.set_small_persistent(True)
+        kg.timing_enable(h, True)
+        fn(h, phi, 200, nc, 1.0, precision=precision)
+        n = kg.timing_read(h)["evolve_launches"]
+        kg.timing_enable(h, False)
+        assert n == nc - 1, (fn.__name__, n)
+        a, b = _both(lambda: fn(h, phi, 200, nc, 1.0, precision=precision))
+        assert _rel(a.reshape(1, -1), b.reshape(1, -1)) < max(tol, TOL_PATHS), fn.__name__
