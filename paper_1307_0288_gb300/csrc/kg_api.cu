@@ -306,9 +306,15 @@ static void term_coef(const Series& ser, int m, int s, double* cr, double* ci) {
 //   buffers q1, q0 (q0 receives q_2), routed to qacc (null = acc[0]).
 // The plain-chain inputs are overwritten from m = 2 on (p_m replaces p_{m-2}).
 template <typename T>
+static kg_status block_norms(kg_hamiltonian* h, int R, const vec2_t<T>* x, int slot);
+
+// norm_slot >= 0: also records ||acc[norm_chain]||^2 per vector in slot norm_slot of
+// h->norms (the unitarity check), inside the cluster launch when that path runs.
+template <typename T>
 static kg_status run_series(kg_hamiltonian* h, int R, const Series& ser, int s, int nch, bool xc,
                             vec2_t<T>* const* in, vec2_t<T>* const* p1, vec2_t<T>* const* acc,
-                            vec2_t<T>* q1, vec2_t<T>* q0, vec2_t<T>* qacc) {
+                            vec2_t<T>* q1, vec2_t<T>* q0, vec2_t<T>* qacc, int norm_slot = -1,
+                            int norm_chain = 0) {
     using V2 = vec2_t<T>;
     PhaseTimer t(h, 1);
     ChainsT<T> ch;
@@ -328,6 +334,10 @@ static kg_status run_series(kg_hamiltonian* h, int R, const Series& ser, int s, 
             ch.acc[k] = acc[k];
         }
         if (xc) ch.qacc = qacc;
+        if (norm_slot >= 0) {
+            cf.norm_chain = norm_chain;
+            cf.norm_out = (double2*)h->norms.p + (size_t)norm_slot * R;
+        }
         KG_CUDA_TRY(launch_evolve_cluster<T>(h->dev, R, nch, xc, plan, cf, ch, h->stream));
         h->counters.evolve_launches += 1;
         h->counters.evolve_site_steps += (double)h->n * R * (nch + (xc ? 1 : 0)) * nterms;
@@ -383,6 +393,7 @@ static kg_status run_series(kg_hamiltonian* h, int R, const Series& ser, int s, 
             qn = qp;
         }
     }
+    if (norm_slot >= 0) KG_TRY(block_norms<T>(h, R, acc[norm_chain], norm_slot));
     return KG_OK;
 }
 
@@ -507,10 +518,10 @@ static kg_status vac_impl(kg_hamiltonian* h, int R, int M, int NC, const Series&
             V2* in[2] = {A, B};
             V2* p1[2] = {VT<T>(h, 5), VT<T>(h, 6)};
             V2* acc[2] = {A2, B2};
-            KG_TRY(run_series<T>(h, R, ser, +1, 2, false, in, p1, acc, nullptr, nullptr, nullptr));
+            // A' = U(-dt) A is chain 0; its norm goes to the next slot
+            KG_TRY(run_series<T>(h, R, ser, +1, 2, false, in, p1, acc, nullptr, nullptr, nullptr, ++slot, 0));
             std::swap(A, A2);
             std::swap(B, B2);
-            KG_TRY(block_norms<T>(h, R, A, ++slot));
         }
         KG_CUDA_TRY(launch_apply<T>(h->dev, R, 2, vscale, A, L, h->stream));   // L = V A
         h->counters.other_launches += 1;
@@ -548,10 +559,10 @@ static kg_status msd_impl(kg_hamiltonian* h, int R, int M, int NC, const Series&
         V2* in[2] = {xi, psi};
         V2* p1[2] = {VT<T>(h, 4), VT<T>(h, 5)};
         V2* acc[2] = {xi2, psi2};
-        KG_TRY(run_series<T>(h, R, ser, -1, 2, true, in, p1, acc, VT<T>(h, 6), VT<T>(h, 7), nullptr));
+        // psi' = U(dt) psi is chain 1; its norm goes to slot t - t0 + 1
+        KG_TRY(run_series<T>(h, R, ser, -1, 2, true, in, p1, acc, VT<T>(h, 6), VT<T>(h, 7), nullptr, t - t0 + 1, 1));
         std::swap(xi, xi2);
         std::swap(psi, psi2);
-        KG_TRY(block_norms<T>(h, R, psi, t - t0 + 1));
         // moments of xi; scratch: the now-free chain buffers 4 and 5
         KG_TRY(kpm_moments<T>(h, R, M, true, xi, xi, VT<T>(h, 4), VT<T>(h, 5), mu + (int64_t)t * M,
                               (int64_t)NC * M));

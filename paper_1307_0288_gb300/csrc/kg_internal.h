@@ -167,6 +167,8 @@ struct SeriesCoef {
     double cr[kClusterMaxTerms + 1] = {0};
     double ci[kClusterMaxTerms + 1] = {0};
     int nterms = 0;
+    int norm_chain = 0;             // chain whose result's squared norm is formed
+    double2* norm_out = nullptr;    // [R] (||acc_r||^2, 0), or null for none
 };
 
 // Chooses the cluster plan of the series kernel for this H, R, nch and xc (cached per

@@ -72,7 +72,10 @@ struct Acc<float> {
 template <int R, int NACC, int NT>
 __device__ __forceinline__ void block_reduce(double (&acc)[NACC], double* __restrict__ dst) {
     constexpr int kWarps = NT / 32;
-    __shared__ double sm[kWarps][32][NACC];
+    constexpr int kLanesUsed = R < 32 ? R : 32;
+    // only the lanes that hold a distinct vector store (the smallest table: the rest of
+    // the SM's unified L1/shared storage stays L1 for the neighbour gathers)
+    __shared__ double sm[kWarps][kLanesUsed][NACC];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if constexpr (R < 32) {
 #pragma unroll
@@ -81,7 +84,6 @@ __device__ __forceinline__ void block_reduce(double (&acc)[NACC], double* __rest
             for (int q = 0; q < NACC; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
         }
     }
-    constexpr int kLanesUsed = R < 32 ? R : 32;
     if (lane < kLanesUsed) {
 #pragma unroll
         for (int q = 0; q < NACC; q++) sm[warp][lane][q] = acc[q];
@@ -95,7 +97,7 @@ __device__ __forceinline__ void block_reduce(double (&acc)[NACC], double* __rest
         for (int q = 0; q < NACC; q++) s[q] = 0.0;
         for (int w = (R < 32 ? 0 : (r >> 5)); w < kWarps; w += kGroups) {
 #pragma unroll
-            for (int q = 0; q < NACC; q++) s[q] += sm[w][r & 31][q];
+            for (int q = 0; q < NACC; q++) s[q] += sm[w][r & (kLanesUsed - 1)][q];
         }
 #pragma unroll
         for (int q = 0; q < NACC; q++) dst[r * NACC + q] = s[q];
@@ -447,6 +449,11 @@ __global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T
 // arithmetic of a term (hop, add_term and their order) is that of evolve_kernel, so the
 // results are bitwise those of the per-term launches.
 // --------------------------------------------------------------------------------
+// With cf.norm_out set, the kernel also forms ||acc_{cf.norm_chain}||^2 of each vector (the
+// unitarity check of the time loops, Eq. 36): per thread in the inner-product arithmetic
+// of the per-step kernels (Acc<T>), merged across lanes by double-float additions, per CTA
+// over its warps in a fixed order, and over the cluster's CTAs by CTA 0 through
+// distributed shared memory in rank order; written as (||x||^2, 0).
 template <typename T, int R, int NCH, bool XC, bool ONSITE, bool YPAR>
 __global__ void __launch_bounds__(512) evolve_cluster_kernel(DevH H, ChainsT<T> ch, SeriesCoef cf, int log_nt) {
     static_assert(R <= kClusterMaxR, "cluster path: at most 16 vectors per block");
@@ -596,6 +603,44 @@ __global__ void __launch_bounds__(512) evolve_cluster_kernel(DevH H, ChainsT<T> 
         if constexpr (XC) {
             if (!q_into_0) ch.qacc[w] = qa;
         }
+    }
+    if (cf.norm_out != nullptr) {
+        // after the chain buffers: [nwarps][R] float2 per-warp sums, then [R] doubles per CTA
+        const int lane = t & 31, warp = t >> 5, nwarps = nt >> 5;
+        float2* wsum = reinterpret_cast<float2*>(sv + NB * 2 * (nt + 1));
+        double* csum = reinterpret_cast<double*>(wsum + nwarps * R);
+        V2 xv = zero;
+#pragma unroll
+        for (int k = 0; k < NCH; k++)
+            if (k == cf.norm_chain) xv = acc[k];
+        Acc<T> a;   // invalid threads hold zeros
+        a.add_prod(xv.x, xv.x);
+        a.add_prod(xv.y, xv.y);
+        float sn = a.s, cn = a.c;
+#pragma unroll
+        for (int off = 16; off >= R; off >>= 1) {
+            const float so = __shfl_xor_sync(0xffffffffu, sn, off), co = __shfl_xor_sync(0xffffffffu, cn, off);
+            df_merge(sn, cn, so, co);
+        }
+        if (lane < R) wsum[warp * R + lane] = make_float2(sn, cn);
+        __syncthreads();
+        if (t < R) {
+            float s2 = 0.0f, c2 = 0.0f;
+            for (int wi = 0; wi < nwarps; wi++) df_merge(s2, c2, wsum[wi * R + t].x, wsum[wi * R + t].y);
+            csum[t] = (double)s2 + (double)c2;
+        }
+        cluster_barrier();   // every CTA's sums are written
+        if (blockIdx.x == 0 && t < R) {
+            const uint32_t local = (uint32_t)__cvta_generic_to_shared(csum + t);
+            double tot = 0.0;
+            for (uint32_t b = 0; b < gridDim.x; b++) {
+                double v;
+                asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(map_cluster_rank(local, b)));
+                tot += v;
+            }
+            cf.norm_out[t] = make_double2(tot, 0.0);
+        }
+        cluster_barrier();   // no CTA exits while CTA 0 still reads its sums
     }
 }
 
@@ -996,6 +1041,11 @@ static int one_wave_grid(K kernel, int64_t n_items, int threads = kThreads) {
     if (it != cache.end()) {
         per_sm = it->second;
     } else {
+        // the grid-stride kernels keep at most a few KB in shared memory: give the rest of
+        // the unified L1/shared storage to L1, which serves the in-chain neighbour gathers
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxL1) != cudaSuccess)
+            cudaGetLastError();
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
             per_sm < 1) {
             cudaGetLastError();
@@ -1263,7 +1313,8 @@ bool evolve_cluster_plan(const DevH& H, int R, int nch, bool xc, ClusterPlan* pl
             const int64_t nt = (int64_t)1 << log_nt;
             const int64_t grid = (items + nt - 1) / nt;
             if (grid < 1 || grid > kMaxCluster) continue;
-            const size_t smem = (size_t)nb * 2 * (size_t)(nt + 1) * sizeof(vec2_t<T>);
+            const size_t smem = (size_t)nb * 2 * (size_t)(nt + 1) * sizeof(vec2_t<T>) +
+                                (size_t)(nt / 32) * R * sizeof(float2) + (size_t)R * sizeof(double);
             if (smem > kClusterSmemBudget) continue;
             ClusterPlan p;
             p.log_nt = log_nt;

@@ -126,24 +126,28 @@ __device__ __forceinline__ uint64_t gelu2(uint64_t z) {
     const float2 uu = f2_unpack(u);
     return f2_fma(hz, f2_pack(tanh_hw(uu.x), tanh_hw(uu.y)), hz);
 }
-// BF16 pair (low = first) of GELU(z0), GELU(z1), for activations that are stored as
-// BF16 anyway (the next layer's tensor-core operand).  The argument u of tanh is formed
-// in FP32 as in gelu2(); then u and z/2 are rounded to BF16 pairs, tanh runs as one
-// packed BF16 SFU instruction for both values (tanh.approx.bf16x2: half the SFU work of
-// two FP32 tanh), and z/2 (1 + tanh u) is one packed BF16 FMA whose single rounding
-// gives the stored pair.  Error: a few BF16 units in the last place of the result
-// (against half a unit when every step before the final rounding is FP32).
+// BF16 pair (low = first) of GELU(z0), GELU(z1).
 __device__ __forceinline__ uint32_t gelu2_bf16(float z0, float z1) {
-    const uint64_t z = f2_pack(z0, z1);
+    const float2 g = f2_unpack(gelu2(f2_pack(z0, z1)));
+    const __nv_bfloat162 b2 = __floats2bfloat162_rn(g.x, g.y);
+    return *(const uint32_t*)&b2;
+}
+
+// 2 GELU(z) = z + z tanh(u) for two values: one packed FMA fewer than gelu2().  The
+// fused inference kernel stores 2 GELU(z) and streams the following layer's weights
+// halved (W/2, an exact power-of-two scaling in BF16), so every product (W/2)(2a) = W a
+// and every FP32 sum of the next layer are bitwise those of W and GELU(z): the network
+// computes exactly what it computed with gelu2() (RN(2x) = 2 RN(x) for normal x).
+__device__ __forceinline__ uint64_t gelu2_twice(uint64_t z) {
     const uint64_t kc = f2_pack(kGeluK * kGeluC, kGeluK * kGeluC), k = f2_pack(kGeluK, kGeluK);
-    const float2 u = f2_unpack(f2_mul(z, f2_fma(kc, f2_mul(z, z), k)));
-    const float2 hz = f2_unpack(f2_mul(f2_pack(0.5f, 0.5f), z));
-    uint32_t ub, hb, tb, r;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(ub) : "f"(u.y), "f"(u.x));     // high half = second value
-    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(tb) : "r"(ub));
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hb) : "f"(hz.y), "f"(hz.x));
-    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(hb), "r"(tb), "r"(hb));
-    return r;
+    const uint64_t u = f2_mul(z, f2_fma(kc, f2_mul(z, z), k));
+    const float2 uu = f2_unpack(u);
+    return f2_fma(z, f2_pack(tanh_hw(uu.x), tanh_hw(uu.y)), z);
+}
+__device__ __forceinline__ uint32_t gelu2_twice_bf16(float z0, float z1) {
+    const float2 g = f2_unpack(gelu2_twice(f2_pack(z0, z1)));
+    const __nv_bfloat162 b2 = __floats2bfloat162_rn(g.x, g.y);
+    return *(const uint32_t*)&b2;
 }
 
 __device__ __forceinline__ float gelu_grad(float z) {
@@ -218,6 +222,24 @@ static kg_status set_smem_once(K kernel, int bytes, std::atomic<unsigned long lo
           "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), \
           "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])                                         \
         : "r"(taddr))
+
+#define KG_TMEM_LD16(taddr, v)                                                                       \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"  \
+                 "%14,%15}, [%16];"                                                                    \
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),  \
+                   "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), \
+                   "=r"(v[14]), "=r"(v[15])                                                            \
+                 : "r"(taddr))
+
+// Waits for this thread's TMEM loads; the registers of v are in-out operands, so no use of
+// them can be scheduled before the wait.
+#define KG_TMEM_WAIT16(v)                                                                            \
+    asm volatile("tcgen05.wait::ld.sync.aligned;"                                                    \
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),  \
+                   "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), \
+                   "+r"(v[14]), "+r"(v[15])                                                            \
+                 :                                                                                     \
+                 : "memory")
 
 #define KG_TMEM_ST32(taddr, v)                                                                       \
     asm volatile(                                                                                    \
@@ -636,8 +658,9 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                             z = f2_fma(f2_pack(w[3 * e + 2], w[3 * e + 5]), f2_pack(xr[i][2], xr[i][2]), z);
                             z = f2_fma(f2_pack(w[3 * e + 1], w[3 * e + 4]), f2_pack(xr[i][1], xr[i][1]), z);
                             z = f2_fma(f2_pack(w[3 * e], w[3 * e + 3]), f2_pack(xr[i][0], xr[i][0]), z);
-                            const float2 zz = f2_unpack(z);
-                            packed[e >> 1] = gelu2_bf16(zz.x, zz.y);
+                            const float2 g = f2_unpack(gelu2_twice(z));   // 2 GELU (W2 streamed halved)
+                            const __nv_bfloat162 b2 = __floats2bfloat162_rn(g.x, g.y);
+                            packed[e >> 1] = *(const uint32_t*)&b2;
                         }
                         st_shared_v4(sA + t * kFTile + (uint32_t)((ch * BM + lane + 32 * i) * 16),
                                      make_uint4(packed[0], packed[1], packed[2], packed[3]));
@@ -661,40 +684,49 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                         continue;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    float ysum = 0.0f;
-#pragma unroll 1
-                    for (int cb = 0; cb < kFCols / 32; cb++) {
-                        const int col0 = grp * kFCols + cb * 32;
-                        uint32_t v[32];
-                        KG_TMEM_LD32(tmem + t * BN + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0, v);
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    // 16-column chunks; the next chunk's TMEM load is in flight while this one's
+                    // GELU runs.  The epilogue stores 2 GELU(z) (layers 3 and 4 stream W/2); the
+                    // output layer sums w5 . 2 GELU(z4) in four partial sums and halves the total.
+                    float ys[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                    const uint32_t trow = tmem + t * BN + ((uint32_t)(quarter * 32) << 16);
+                    constexpr int kChunk16 = kFCols / 16;
+                    uint32_t va[16], vb[16];
+                    KG_TMEM_LD16(trow + (uint32_t)(grp * kFCols), va);
+                    KG_TMEM_WAIT16(va);
+#pragma unroll
+                    for (int cb = 0; cb < kChunk16; cb++) {
+                        const int col0 = grp * kFCols + cb * 16;
+                        uint32_t* v = (cb & 1) ? vb : va;
+                        uint32_t* vn = (cb & 1) ? va : vb;
+                        if (cb + 1 < kChunk16) KG_TMEM_LD16(trow + (uint32_t)(col0 + 16), vn);
                         if (l == 2) {
-                            // output layer on the FP32 activations: y = w5 . GELU(z4) + b5
                             const float4* w54 = (const float4*)(w5 + col0);
 #pragma unroll
-                            for (int q = 0; q < 8; q++) {
+                            for (int q = 0; q < 4; q++) {
                                 const float4 f = __ldg(w54 + q);
-                                const float2 g0 = f2_unpack(gelu2(f2_pack(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]))));
+                                const float2 g0 = f2_unpack(gelu2_twice(f2_pack(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]))));
                                 const float2 g1 =
-                                    f2_unpack(gelu2(f2_pack(__uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]))));
-                                ysum = fmaf(g0.x, f.x, ysum);
-                                ysum = fmaf(g0.y, f.y, ysum);
-                                ysum = fmaf(g1.x, f.z, ysum);
-                                ysum = fmaf(g1.y, f.w, ysum);
+                                    f2_unpack(gelu2_twice(f2_pack(__uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]))));
+                                ys[0] = fmaf(g0.x, f.x, ys[0]);
+                                ys[1] = fmaf(g0.y, f.y, ys[1]);
+                                ys[2] = fmaf(g1.x, f.z, ys[2]);
+                                ys[3] = fmaf(g1.y, f.w, ys[3]);
                             }
                         } else {
 #pragma unroll
-                            for (int c8 = 0; c8 < 4; c8++) {
+                            for (int c8 = 0; c8 < 2; c8++) {
                                 uint32_t packed[4];
 #pragma unroll
                                 for (int e = 0; e < 8; e += 2)
-                                    packed[e >> 1] = gelu2_bf16(__uint_as_float(v[c8 * 8 + e]), __uint_as_float(v[c8 * 8 + e + 1]));
+                                    packed[e >> 1] = gelu2_twice_bf16(__uint_as_float(v[c8 * 8 + e]), __uint_as_float(v[c8 * 8 + e + 1]));
                                 const int chunk = (col0 >> 3) + c8;
                                 st_shared_v4(sA + t * kFTile + (uint32_t)((chunk * BM + rl) * 16),
                                              make_uint4(packed[0], packed[1], packed[2], packed[3]));
                             }
                         }
+                        if (cb + 1 < kChunk16) KG_TMEM_WAIT16(vn);
                     }
+                    const float ysum = 0.5f * ((ys[0] + ys[1]) + (ys[2] + ys[3]));
                     if (l < 2) {
                         preload_bias(t, l + 3);
                         publish(t);
@@ -893,8 +925,10 @@ __global__ void cast_weights_kernel(const float* __restrict__ p, __nv_bfloat16* 
         const __nv_bfloat16 b = __float2bfloat16_rn(p[layer_w(l + 2) + rem]);
         w[k] = b;
         wt[(int64_t)l * H * H + (int64_t)i * H + o] = b;
-        // tiled: [32 k-chunks][256 rows][8], row = output unit o, k = input i
-        wtile[(int64_t)l * H * H + ((int64_t)(i >> 3) * H + o) * 8 + (i & 7)] = b;
+        // tiled: [32 k-chunks][256 rows][8], row = output unit o, k = input i.  Halved (exactly):
+        // the fused inference kernel feeds these layers 2 GELU(z) (gelu2_twice)
+        wtile[(int64_t)l * H * H + ((int64_t)(i >> 3) * H + o) * 8 + (i & 7)] =
+            __float2bfloat16_rn(0.5f * p[layer_w(l + 2) + rem]);
     }
 }
 

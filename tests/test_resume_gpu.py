@@ -48,16 +48,23 @@ def test_vac_resume_reproduces_one_run(precision):
     assert np.array_equal(mu2, one[:, 2:5])
 
 
-def test_norm_drift_is_reported():
-    """bessel_tol = 0.5 keeps only J_0 .. J_3 of U(dt) at tau = 3.15: far from unitary."""
+@pytest.mark.parametrize("cluster", [True, False])
+def test_norm_drift_is_reported(cluster):
+    """bessel_tol = 0.5 keeps only J_0 .. J_3 of U(dt) at tau = 3.15: far from unitary.
+    Both ways of forming the norms: inside the small-instance series launch (cluster)
+    and by separate inner-product launches (one launch per step)."""
     w = ki.sheet_cells(16, 16, vacancy_conc=0.02)
     h = kg.from_workload(w)
     phi = w.vectors(2)
-    for fn in (kg.msd, kg.vac):
-        with pytest.raises(kg.KgError) as e:
-            fn(h, phi, 64, 3, 1.0, bessel_tol=0.5)
-        assert e.value.status == -5 and "norm drift" in str(e.value)
-    assert np.all(np.isfinite(kg.msd(h, phi, 64, 3, 1.0)))
+    try:
+        kg.set_small_persistent(cluster)
+        for fn in (kg.msd, kg.vac):
+            with pytest.raises(kg.KgError) as e:
+                fn(h, phi, 64, 3, 1.0, bessel_tol=0.5)
+            assert e.value.status == -5 and "norm drift" in str(e.value)
+        assert np.all(np.isfinite(kg.msd(h, phi, 64, 3, 1.0)))
+    finally:
+        kg.set_small_persistent(True)
 
 
 def test_allocation_cap_gives_enomem():

@@ -198,11 +198,17 @@ def test_vac_and_msd_time_loops_one_series_launch_per_time_step(precision, tol):
     phi = w.vectors(1)
     nc = 6
     for fn in (kg.vac, kg.msd):
+        counts = {}
+        for cluster in (True, False):
+            kg.set_small_persistent(cluster)
+            kg.timing_enable(h, True)
+            fn(h, phi, 200, nc, 1.0, precision=precision)
+            counts[cluster] = kg.timing_read(h)
+            kg.timing_enable(h, False)
         kg.set_small_persistent(True)
-        kg.timing_enable(h, True)
-        fn(h, phi, 200, nc, 1.0, precision=precision)
-        n = kg.timing_read(h)["evolve_launches"]
-        kg.timing_enable(h, False)
-        assert n == nc - 1, (fn.__name__, n)
+        assert counts[True]["evolve_launches"] == nc - 1, (fn.__name__, counts[True])
+        # the unitarity norms of the nc - 1 steps come with the series launch (no inner-product
+        # and reduction launches)
+        assert counts[False]["other_launches"] - counts[True]["other_launches"] == 2 * (nc - 1), fn.__name__
         a, b = _both(lambda: fn(h, phi, 200, nc, 1.0, precision=precision))
         assert _rel(a.reshape(1, -1), b.reshape(1, -1)) < max(tol, TOL_PATHS), fn.__name__
