@@ -211,6 +211,42 @@ static kg_status kpm_moments(kg_hamiltonian* h, int R, int M, bool sym, const ve
     double* pf = (double*)h->part_first.p;
     double* ring = (double*)h->part_ring.p;
     cudaStream_t s = h->stream;
+    if (cluster) {
+        // small instance: the first step and up to a chunk of further steps per cluster launch,
+        // vectors in shared memory.  The chunk's last phi_n and phi_{n-1} land where the
+        // per-step loop's rotation would put them: after the first step (phi_1 into b1,
+        // phi_0 staying in phi_r) every later step writes in place over phi_{n-1}.
+        static_assert(kClusterMaxChunk <= kRing, "a chunk's partial slabs must fit the ring");
+        const int total = steps + 1;   // the first step and the `steps` further ones
+        const V2* cur = phi_r;
+        const V2* prev = nullptr;
+        V2* out = b1;
+        for (int n0 = 0; n0 < total;) {
+            const bool first = n0 == 0;
+            const int room = plan.chunk - ((first && !sym) ? 1 : 0);
+            const int cnt = std::min(room, total - n0);
+            const V2* src_cur = cur;
+            const V2* src_prev = prev;
+            for (int k = 0; k < cnt; k++) {   // the per-step loop's rotation, replayed on the host
+                const int n = n0 + k;
+                const V2* new_cur = out;
+                prev = cur;
+                out = n == 0 ? b0 : const_cast<V2*>(cur);
+                cur = new_cur;
+            }
+            // cnt >= 2 whenever the chunk starts with the first step (steps > 0), so its final
+            // phi_n and phi_{n-1} are both in b0 / b1 and phi_r is never written
+            KG_CUDA_TRY(launch_kpm_cluster<T>(h->dev, R, sym, plan, phi_l, src_cur, src_prev, const_cast<V2*>(cur),
+                                              const_cast<V2*>(prev), ring, cnt, first, s));
+            KG_CUDA_TRY(launch_reduce_ring(ring, 0, cnt + ((first && !sym) ? 1 : 0), kRing, plan.grid, R, sym, n0,
+                                           mu, r_stride, M, s, first));
+            h->counters.kpm_launches += 1;
+            h->counters.other_launches += 1;
+            h->counters.kpm_site_steps += (double)h->n * R * cnt;
+            n0 += cnt;
+        }
+        return KG_OK;
+    }
     // first step: phi_1 = H~ phi_0 (into b1), moments 0 and 1
     if (sym) KG_CUDA_TRY(launch_kpm_sym<T>(h->dev, R, true, phi_r, nullptr, b1, pf, grid, s));
     else KG_CUDA_TRY(launch_kpm_gen<T>(h->dev, R, true, phi_l, phi_r, nullptr, b1, pf, grid, s));
@@ -222,25 +258,6 @@ static kg_status kpm_moments(kg_hamiltonian* h, int R, int M, bool sym, const ve
     const V2* cur = b1;
     const V2* prev = phi_r;
     V2* out = b0;
-    if (cluster) {
-        // small instance: each chunk of steps in one cluster launch, vectors in shared memory
-        static_assert(kClusterMaxChunk <= kRing, "a chunk's partial slabs must fit the ring");
-        for (int n0 = 1; n0 <= steps; n0 += plan.chunk) {
-            const int cnt = std::min(plan.chunk, steps - n0 + 1);
-            KG_CUDA_TRY(launch_kpm_cluster<T>(h->dev, R, sym, plan, phi_l, cur, prev, out, ring, cnt, s));
-            KG_CUDA_TRY(launch_reduce_ring(ring, 0, cnt, kRing, plan.grid, R, sym, n0, mu, r_stride, M, s));
-            h->counters.kpm_launches += 1;
-            h->counters.other_launches += 1;
-            h->counters.kpm_site_steps += (double)h->n * R * cnt;
-            for (int k = 0; k < cnt; k++) {   // the kernel's pointer rotation, replayed on the host
-                const V2* new_cur = out;
-                prev = cur;
-                out = const_cast<V2*>(cur);
-                cur = new_cur;
-            }
-        }
-        return KG_OK;
-    }
     int pending = 0, first_pending = 1;
     for (int n = 1; n <= steps; n++) {
         double* slab = ring + (int64_t)((n - 1) % kRing) * grid * R * 2;

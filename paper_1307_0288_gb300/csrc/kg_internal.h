@@ -125,15 +125,17 @@ struct ClusterPlan {
 template <typename T>
 bool kpm_cluster_plan(const DevH& H, int R, bool sym, ClusterPlan* plan);
 
-// The non-first KPM steps n0 .. n0 + nsteps - 1 (nsteps <= plan.chunk) in one cluster
-// launch: the per-step kernels' vectors (bitwise), and per step k the per-CTA partial
-// sums in ring slab k, laid out [k][plan.grid][R][2] like theirs.  cur / prev / out are
-// the blocks of the first of these steps; phi_n and phi_{n-1} are left in the blocks the
-// per-step loop's pointer rotation would leave them in.
+// KPM steps n0 .. n0 + nsteps - 1 in one cluster launch: the per-step kernels' vectors
+// (bitwise), and per step k the per-CTA partial sums in ring slab k, laid out
+// [k][plan.grid][R][2] like theirs.  phi_n and phi_{n-1} of step n0 are read from src_cur
+// and src_prev; after the last step phi_n and phi_{n-1} are written to dst_cur and
+// dst_prev.  first: step n0 = 0 is the first step (src_prev unused); the general
+// recursion then also writes <L|phi_0> to slab nsteps (nsteps + 1 <= plan.chunk).
 template <typename T>
 cudaError_t launch_kpm_cluster(const DevH& H, int R, bool sym, const ClusterPlan& plan,
-                               const vec2_t<T>* L, const vec2_t<T>* cur, const vec2_t<T>* prev,
-                               vec2_t<T>* out, double* ring, int nsteps, cudaStream_t s);
+                               const vec2_t<T>* L, const vec2_t<T>* src_cur, const vec2_t<T>* src_prev,
+                               vec2_t<T>* dst_cur, vec2_t<T>* dst_prev, double* ring, int nsteps, bool first,
+                               cudaStream_t s);
 
 // Reduce per-block partials of a KPM run into moments mu[r * r_stride + n].
 //   first: partial [grid][R][A] of the first step (A = 2 sym, 4 gen)
@@ -142,7 +144,7 @@ cudaError_t launch_reduce_first(const double* partial, int grid, int R, bool sym
                                 double2* mu, int64_t r_stride, int M, cudaStream_t s);
 cudaError_t launch_reduce_ring(const double* ring, int slab0, int nslab, int ring_size,
                                int grid, int R, bool sym, int n0, double2* mu,
-                               int64_t r_stride, int M, cudaStream_t s);
+                               int64_t r_stride, int M, cudaStream_t s, bool first = false);
 
 template <typename T>
 struct ChainsT {

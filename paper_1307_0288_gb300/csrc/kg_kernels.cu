@@ -326,18 +326,25 @@ __device__ __forceinline__ void df_merge(float& s, float& c, float s2, float c2)
 
 constexpr int kClusterMaxR = 16;   // vectors per block the cluster path takes
 
+// first = 1: the chunk starts with the first recursion step (phi_1 = H~ phi_0 with the
+// hopping h, no phi_{-1} term: the per-step kernels' FIRST arithmetic), whose partial sums
+// go to ring slab 0 like any step's (for the general recursion, <L|phi_0> goes to the
+// extra slab nsteps).  The chunk reads its phi_n and phi_{n-1} from src_cur / src_prev
+// (src_prev unused when first) and leaves its last phi_n and phi_{n-1} in dst_cur /
+// dst_prev, the blocks the per-step loop's pointer rotation would leave them in.
 template <typename T, int R, bool ONSITE, bool SYM>
 __global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T>* __restrict__ L,
-                                                         const vec2_t<T>* cur_g, const vec2_t<T>* prev_g,
-                                                         vec2_t<T>* out_g, double* __restrict__ ring,
-                                                         int nsteps, int log_nt) {
+                                                         const vec2_t<T>* src_cur, const vec2_t<T>* src_prev,
+                                                         vec2_t<T>* dst_cur, vec2_t<T>* dst_prev,
+                                                         double* __restrict__ ring, int nsteps, int log_nt,
+                                                         int first) {
     static_assert(R <= kClusterMaxR, "cluster path: at most 16 vectors per block");
     using V2 = vec2_t<T>;
     extern __shared__ __align__(16) unsigned char kg_cluster_smem[];
     const int nt = 1 << log_nt;
     const int nwarps = nt >> 5;
     V2* sv = reinterpret_cast<V2*>(kg_cluster_smem);                    // [2][nt + 1]
-    float4* wp = reinterpret_cast<float4*>(sv + 2 * (nt + 1));          // [nsteps][nwarps][R]
+    float4* wp = reinterpret_cast<float4*>(sv + 2 * (nt + 1));          // [nsteps (+1)][nwarps][R]
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int r = t & (R - 1);
     const int64_t n_items = H.n * R;
@@ -346,8 +353,8 @@ __global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T
     const V2 zero = mk<T>(0, 0);
 
     // own items of phi_n (buffer 0) and phi_{n-1} (buffer 1), and the zero entries
-    sv[t] = valid ? cur_g[w] : zero;
-    sv[nt + 1 + t] = valid ? prev_g[w] : zero;
+    sv[t] = valid ? src_cur[w] : zero;
+    sv[nt + 1 + t] = (valid && !first) ? src_prev[w] : zero;
     if (t == 0) {
         sv[nt] = zero;
         sv[2 * nt + 1] = zero;
@@ -368,16 +375,23 @@ __global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T
             na[q] = map_cluster_rank(base + slot * (uint32_t)sizeof(V2), rank);
         }
     }
-    T e = 0;
-    if constexpr (ONSITE) e = valid ? (T)(2.0 * __ldg(H.onsite + n)) : (T)0;
+    T e1 = 0, e2 = 0;
+    if constexpr (ONSITE) {
+        const double o = valid ? __ldg(H.onsite + n) : 0.0;
+        e1 = (T)(1.0 * o);
+        e2 = (T)(2.0 * o);
+    }
     V2 l = zero;
     if constexpr (!SYM) l = valid ? __ldg(L + w) : zero;
-    const T c = (T)(2.0 * H.h);
+    const T c1 = (T)H.h, c2 = (T)(2.0 * H.h);
     const uint32_t boff = (uint32_t)((nt + 1) * sizeof(V2));
     cluster_barrier();   // every CTA's buffers are filled before any peer reads them
 
     int cb = 0;   // buffer holding phi_n
     for (int k = 0; k < nsteps; k++) {
+        const bool fs = first && k == 0;
+        const T c = fs ? c1 : c2;
+        const T e = fs ? e1 : e2;
         const uint32_t o = cb ? boff : 0u;
         V2 ga, gb, gc;
         ld_cluster(na[0] + o, ga);
@@ -386,7 +400,7 @@ __global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T
         V2* curb = sv + cb * (nt + 1);
         V2* prvb = sv + (cb ^ 1) * (nt + 1);
         const V2 x = curb[t];
-        const V2 z = prvb[t];
+        const V2 z = fs ? zero : prvb[t];
         const T yr = hop<T>(c, ga.x, gb.x, gc.x, e, x.x, z.x, ONSITE);
         const T yi = hop<T>(c, ga.y, gb.y, gc.y, e, x.y, z.y, ONSITE);
         if (valid) prvb[t] = mk<T>(yr, yi);
@@ -402,29 +416,45 @@ __global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T
             a1.add_prod(l.x, yi);
             a1.add_prod(-l.y, yr);
         }
-        float s0 = a0.s, c0 = a0.c, s1 = a1.s, c1 = a1.c;
+        float s0 = a0.s, c0 = a0.c, s1 = a1.s, c1s = a1.c;
 #pragma unroll
         for (int off = 16; off >= R; off >>= 1) {
             const float s0o = __shfl_xor_sync(0xffffffffu, s0, off), c0o = __shfl_xor_sync(0xffffffffu, c0, off);
-            const float s1o = __shfl_xor_sync(0xffffffffu, s1, off), c1o = __shfl_xor_sync(0xffffffffu, c1, off);
+            const float s1o = __shfl_xor_sync(0xffffffffu, s1, off), c1o = __shfl_xor_sync(0xffffffffu, c1s, off);
             df_merge(s0, c0, s0o, c0o);
-            df_merge(s1, c1, s1o, c1o);
+            df_merge(s1, c1s, s1o, c1o);
         }
-        if (lane < R) wp[((int64_t)k * nwarps + warp) * R + lane] = make_float4(s0, c0, s1, c1);
+        if (lane < R) wp[((int64_t)k * nwarps + warp) * R + lane] = make_float4(s0, c0, s1, c1s);
+        if constexpr (!SYM) {
+            if (fs) {
+                // <L|phi_0> of the first step, kept as step nsteps
+                Acc<T> b0, b1;
+                b0.add_prod(l.x, x.x);
+                b0.add_prod(l.y, x.y);
+                b1.add_prod(l.x, x.y);
+                b1.add_prod(-l.y, x.x);
+                float u0 = b0.s, v0 = b0.c, u1 = b1.s, v1 = b1.c;
+#pragma unroll
+                for (int off = 16; off >= R; off >>= 1) {
+                    const float u0o = __shfl_xor_sync(0xffffffffu, u0, off), v0o = __shfl_xor_sync(0xffffffffu, v0, off);
+                    const float u1o = __shfl_xor_sync(0xffffffffu, u1, off), v1o = __shfl_xor_sync(0xffffffffu, v1, off);
+                    df_merge(u0, v0, u0o, v0o);
+                    df_merge(u1, v1, u1o, v1o);
+                }
+                if (lane < R) wp[((int64_t)nsteps * nwarps + warp) * R + lane] = make_float4(u0, v0, u1, v1);
+            }
+        }
         cluster_barrier();
         cb ^= 1;
-        const vec2_t<T>* next = out_g;   // the per-step loop's rotation of the global blocks
-        prev_g = cur_g;
-        out_g = const_cast<vec2_t<T>*>(cur_g);
-        cur_g = next;
     }
     // no peer reads this CTA's buffers any more; write phi_n and phi_{n-1} back
     if (valid) {
-        const_cast<vec2_t<T>*>(cur_g)[w] = sv[cb * (nt + 1) + t];
-        const_cast<vec2_t<T>*>(prev_g)[w] = sv[(cb ^ 1) * (nt + 1) + t];
+        dst_cur[w] = sv[cb * (nt + 1) + t];
+        dst_prev[w] = sv[(cb ^ 1) * (nt + 1) + t];
     }
     // cross-warp sums per (step, vector, product), fixed order, into ring slab k
-    for (int i = t; i < nsteps * R * 2; i += nt) {
+    const int nslab = nsteps + ((!SYM && first) ? 1 : 0);
+    for (int i = t; i < nslab * R * 2; i += nt) {
         const int k = i / (2 * R), rr = (i >> 1) & (R - 1), q = i & 1;
         float s = 0.0f, cc = 0.0f;
         for (int wi = 0; wi < nwarps; wi++) {
@@ -811,20 +841,34 @@ __global__ void reduce_first_kernel(const double* __restrict__ part, int grid, i
     }
 }
 
+// first = 1 (slab slab0 holds the first step, n0 = 0): the first step's sums are the
+// moments themselves (mu_0 = S0(0), mu_1 = S1(0) with doubling; mu_1 = <L|phi_1>), every
+// block re-reduces slab slab0 for mu_0 and mu_1 instead of reading them back (no order
+// between the blocks of one launch), and for the general recursion the last block's
+// slab holds <L|phi_0> = mu_0.
 __global__ void reduce_ring_kernel(const double* __restrict__ ring, int slab0, int ring_size,
                                    int grid, int R, int sym, int n0, double2* mu, int64_t r_stride,
-                                   int M) {
+                                   int M, int first) {
     __shared__ double res[kThreads];
+    __shared__ double res0[kThreads];
     const int slab = (slab0 + blockIdx.x) % ring_size;
     const int n = n0 + blockIdx.x;   // recursion step that produced this slab
     reduce_blocks(ring + (int64_t)slab * grid * R * 2, grid, R, 2, res);
+    if (first && sym) reduce_blocks(ring + (int64_t)(slab0 % ring_size) * grid * R * 2, grid, R, 2, res0);
     if (threadIdx.x < R) {
         const int r = threadIdx.x;
         double2* m = mu + r * r_stride;
         if (sym) {
-            const double mu0 = m[0].x, mu1 = m[1].x;
-            if (2 * n < M) m[2 * n] = make_double2(2.0 * res[r * 2] - mu0, 0.0);
-            if (2 * n + 1 < M) m[2 * n + 1] = make_double2(2.0 * res[r * 2 + 1] - mu1, 0.0);
+            if (first && n == 0) {
+                m[0] = make_double2(res[r * 2], 0.0);
+                if (M > 1) m[1] = make_double2(res[r * 2 + 1], 0.0);
+            } else {
+                const double mu0 = first ? res0[r * 2] : m[0].x, mu1 = first ? res0[r * 2 + 1] : m[1].x;
+                if (2 * n < M) m[2 * n] = make_double2(2.0 * res[r * 2] - mu0, 0.0);
+                if (2 * n + 1 < M) m[2 * n + 1] = make_double2(2.0 * res[r * 2 + 1] - mu1, 0.0);
+            }
+        } else if (first && blockIdx.x == gridDim.x - 1) {
+            m[0] = make_double2(res[r * 2], res[r * 2 + 1]);   // <L|phi_0>
         } else {
             if (n + 1 < M) m[n + 1] = make_double2(res[r * 2], res[r * 2 + 1]);
         }
@@ -1196,13 +1240,15 @@ static cudaError_t launch_single_cluster(void (*kernel)(KArgs...), int grid, int
 
 template <typename T>
 static cudaError_t kpm_cluster_dispatch(const DevH& H, int R, bool sym, const ClusterPlan& p, bool query,
-                                        const vec2_t<T>* L, const vec2_t<T>* cur, const vec2_t<T>* prev,
-                                        vec2_t<T>* out, double* ring, int nsteps, cudaStream_t s) {
+                                        const vec2_t<T>* L, const vec2_t<T>* src_cur, const vec2_t<T>* src_prev,
+                                        vec2_t<T>* dst_cur, vec2_t<T>* dst_prev, double* ring, int nsteps,
+                                        bool first, cudaStream_t s) {
     const bool ons = H.onsite != nullptr;
     cudaError_t e = cudaErrorNotSupported;
     KG_DISPATCH_R16(R, KG_BOOL(ons, ON, KG_BOOL(sym, SY,
         e = launch_single_cluster(kpm_cluster_kernel<T, RR, ON, SY>, p.grid, 1 << p.log_nt, p.smem, query, s, H,
-                                  L, cur, prev, out, ring, nsteps, p.log_nt))));
+                                  L, src_cur, src_prev, dst_cur, dst_prev, ring, nsteps, p.log_nt,
+                                  first ? 1 : 0))));
     return e;
 }
 
@@ -1244,7 +1290,7 @@ bool kpm_cluster_plan(const DevH& H, int R, bool sym, ClusterPlan* plan) {
             p.chunk = (int)std::min<size_t>(kClusterMaxChunk, (kClusterSmemBudget - vec) / per_step);
             p.smem = vec + (size_t)p.chunk * per_step;
             const cudaError_t e = kpm_cluster_dispatch<T>(H, R, sym, p, true, nullptr, nullptr, nullptr, nullptr,
-                                                          nullptr, 0, nullptr);
+                                                          nullptr, nullptr, 0, false, nullptr);
             if (e != cudaSuccess) cudaGetLastError();   // a refused query must not leak into later launch checks
             else best = p;
         }
@@ -1256,11 +1302,13 @@ bool kpm_cluster_plan(const DevH& H, int R, bool sym, ClusterPlan* plan) {
 
 template <typename T>
 cudaError_t launch_kpm_cluster(const DevH& H, int R, bool sym, const ClusterPlan& p, const vec2_t<T>* L,
-                               const vec2_t<T>* cur, const vec2_t<T>* prev, vec2_t<T>* out, double* ring,
-                               int nsteps, cudaStream_t s) {
+                               const vec2_t<T>* src_cur, const vec2_t<T>* src_prev, vec2_t<T>* dst_cur,
+                               vec2_t<T>* dst_prev, double* ring, int nsteps, bool first, cudaStream_t s) {
     if (nsteps <= 0) return cudaSuccess;
-    if (nsteps > p.chunk || p.grid < 1) return cudaErrorInvalidValue;
-    return kpm_cluster_dispatch<T>(H, R, sym, p, false, L, cur, prev, out, ring, nsteps, s);
+    // the general recursion's first chunk keeps <L|phi_0> as one more step's partial sums
+    if (nsteps + ((first && !sym) ? 1 : 0) > p.chunk || p.grid < 1) return cudaErrorInvalidValue;
+    return kpm_cluster_dispatch<T>(H, R, sym, p, false, L, src_cur, src_prev, dst_cur, dst_prev, ring, nsteps,
+                                   first, s);
 }
 
 template <typename T>
@@ -1396,10 +1444,10 @@ cudaError_t launch_reduce_first(const double* partial, int grid, int R, bool sym
 
 cudaError_t launch_reduce_ring(const double* ring, int slab0, int nslab, int ring_size, int grid,
                                int R, bool sym, int n0, double2* mu, int64_t r_stride, int M,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool first) {
     if (nslab <= 0) return cudaSuccess;
     reduce_ring_kernel<<<nslab, kThreads, 0, s>>>(ring, slab0, ring_size, grid, R, sym ? 1 : 0,
-                                                  n0, mu, r_stride, M);
+                                                  n0, mu, r_stride, M, first ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1477,7 +1525,7 @@ cudaError_t launch_to_c64(const double2* in, float2* out, int64_t n_items, cudaS
     template bool kpm_cluster_plan<T>(const DevH&, int, bool, ClusterPlan*);                       \
     template cudaError_t launch_kpm_cluster<T>(const DevH&, int, bool, const ClusterPlan&,         \
                                                const vec2_t<T>*, const vec2_t<T>*, const vec2_t<T>*, \
-                                               vec2_t<T>*, double*, int, cudaStream_t);             \
+                                               vec2_t<T>*, vec2_t<T>*, double*, int, bool, cudaStream_t); \
     template bool evolve_cluster_plan<T>(const DevH&, int, int, bool, ClusterPlan*);                \
     template cudaError_t launch_evolve_cluster<T>(const DevH&, int, int, bool, const ClusterPlan&,   \
                                                   const SeriesCoef&, const ChainsT<T>&, cudaStream_t); \

@@ -208,7 +208,10 @@ def test_vac_and_msd_time_loops_one_series_launch_per_time_step(precision, tol):
         kg.set_small_persistent(True)
         assert counts[True]["evolve_launches"] == nc - 1, (fn.__name__, counts[True])
         # the unitarity norms of the nc - 1 steps come with the series launch (no inner-product
-        # and reduction launches)
-        assert counts[False]["other_launches"] - counts[True]["other_launches"] == 2 * (nc - 1), fn.__name__
+        # and reduction launches), and each moment loop's first step with its first cluster
+        # launch (no separate first-step reduction): VAC has nc moment loops, MSD nc - 1
+        loops = nc if fn is kg.vac else nc - 1
+        assert counts[False]["other_launches"] - counts[True]["other_launches"] == 2 * (nc - 1) + loops, fn.__name__
+        assert counts[True]["kpm_launches"] == loops * math.ceil((200 - 1 if fn is kg.vac else 100) / 256)
         a, b = _both(lambda: fn(h, phi, 200, nc, 1.0, precision=precision))
         assert _rel(a.reshape(1, -1), b.reshape(1, -1)) < max(tol, TOL_PATHS), fn.__name__
