@@ -533,8 +533,9 @@ def run_batched(args):
     work = float(n_sites) * rv * steps_per_call * args.steps * world
     paper_work = float(n_sites) * rv * (mm - 1) * args.steps * world
     step_ms = ms / args.steps / steps_per_call
-    # Anderson disorder adds the on-site term e x: one more DFMA per item (14 flops)
-    flops = (KPM_FP64_FLOPS_PER_ITEM + 2) * n_sites * rv
+    # Anderson disorder adds the on-site term e x: y = c (a + b + d) + e x - z costs 4 FMA per
+    # real component, 8 DFMA = 16 flops per complex item
+    flops = (KPM_FP64_FLOPS_PER_ITEM + 4) * n_sites * rv
     achieved = flops / (step_ms * 1e-3) / 1e12
     bytes_step = n_sites * (12 + 8 + 48 * rv)
     peaks = _peaks()

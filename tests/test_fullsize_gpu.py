@@ -160,3 +160,19 @@ def test_mlp_forward_batch_1m_sampled_and_permutation_invariant():
     y2 = torch.zeros(n, dtype=torch.float32, device="cuda")
     net.forward(xd[perm].contiguous(), out=y2)
     assert torch.equal(y2, y[perm])
+
+
+def test_dos_3000_moments_bench_sheet_all_moments():
+    """The benchmark's sheet and launch configuration (2048 x 1024 sites, 0.5 % vacancies,
+    4 vectors, M = 3000): every one of the 3000 DOS moments of vector 0 against the oracle's
+    plain recursion, so the high-order moments of the doubling identity are pinned at full
+    size (about 45 s of single-thread oracle time)."""
+    w = ki.sheet_cells(1024, 512, vacancy_conc=0.005, n_vec=4)
+    h = kg.from_workload(w)
+    phi = w.vectors(4)
+    got = kg.dos_moments(h, phi, 3000)
+    ho = oracle.from_workload(w)
+    want = oracle.kpm_moments(ho, phi[:, 0], phi[:, 0], 3000)
+    assert _rel(got[0], want) < TOL_MOMENTS
+    tail = slice(2990, 3000)
+    assert _rel(got[0, tail], want[tail]) < 1e-8
