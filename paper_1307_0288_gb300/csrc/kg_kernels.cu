@@ -387,21 +387,6 @@ __global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T
     const uint32_t boff = (uint32_t)((nt + 1) * sizeof(V2));
     cluster_barrier();   // every CTA's buffers are filled before any peer reads them
 
-    // Lane merge of a step's per-thread sums across the lanes holding the same vector
-    // (double-float additions), stored per warp.  Step k's merge runs in step k + 1 after
-    // that step's neighbour gathers are issued, so it overlaps their latency.
-    auto merge_store = [&](float s0, float c0, float s1, float c1s, int k) {
-#pragma unroll
-        for (int off = 16; off >= R; off >>= 1) {
-            const float s0o = __shfl_xor_sync(0xffffffffu, s0, off), c0o = __shfl_xor_sync(0xffffffffu, c0, off);
-            const float s1o = __shfl_xor_sync(0xffffffffu, s1, off), c1o = __shfl_xor_sync(0xffffffffu, c1s, off);
-            df_merge(s0, c0, s0o, c0o);
-            df_merge(s1, c1s, s1o, c1o);
-        }
-        if (lane < R) wp[((int64_t)k * nwarps + warp) * R + lane] = make_float4(s0, c0, s1, c1s);
-    };
-    float ps0 = 0.0f, pc0 = 0.0f, ps1 = 0.0f, pc1 = 0.0f;   // the previous step's unmerged sums
-
     int cb = 0;   // buffer holding phi_n
     for (int k = 0; k < nsteps; k++) {
         const bool fs = first && k == 0;
@@ -412,7 +397,6 @@ __global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T
         ld_cluster(na[0] + o, ga);
         ld_cluster(na[1] + o, gb);
         ld_cluster(na[2] + o, gc);
-        if (k > 0) merge_store(ps0, pc0, ps1, pc1, k - 1);
         V2* curb = sv + cb * (nt + 1);
         V2* prvb = sv + (cb ^ 1) * (nt + 1);
         const V2 x = curb[t];
@@ -432,10 +416,15 @@ __global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T
             a1.add_prod(l.x, yi);
             a1.add_prod(-l.y, yr);
         }
-        ps0 = a0.s;
-        pc0 = a0.c;
-        ps1 = a1.s;
-        pc1 = a1.c;
+        float s0 = a0.s, c0 = a0.c, s1 = a1.s, c1s = a1.c;
+#pragma unroll
+        for (int off = 16; off >= R; off >>= 1) {
+            const float s0o = __shfl_xor_sync(0xffffffffu, s0, off), c0o = __shfl_xor_sync(0xffffffffu, c0, off);
+            const float s1o = __shfl_xor_sync(0xffffffffu, s1, off), c1o = __shfl_xor_sync(0xffffffffu, c1s, off);
+            df_merge(s0, c0, s0o, c0o);
+            df_merge(s1, c1s, s1o, c1o);
+        }
+        if (lane < R) wp[((int64_t)k * nwarps + warp) * R + lane] = make_float4(s0, c0, s1, c1s);
         if constexpr (!SYM) {
             if (fs) {
                 // <L|phi_0> of the first step, kept as step nsteps
@@ -458,13 +447,11 @@ __global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T
         cluster_barrier();
         cb ^= 1;
     }
-    if (nsteps > 0) merge_store(ps0, pc0, ps1, pc1, nsteps - 1);
     // no peer reads this CTA's buffers any more; write phi_n and phi_{n-1} back
     if (valid) {
         dst_cur[w] = sv[cb * (nt + 1) + t];
         dst_prev[w] = sv[(cb ^ 1) * (nt + 1) + t];
     }
-    __syncthreads();   // every warp's merged sums are in wp before the cross-warp sums
     // cross-warp sums per (step, vector, product), fixed order, into ring slab k
     const int nslab = nsteps + ((!SYM && first) ? 1 : 0);
     for (int i = t; i < nslab * R * 2; i += nt) {
