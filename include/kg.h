@@ -201,7 +201,10 @@ kg_status kg_msd(kg_hamiltonian* h, const kg_run* run, const double* phi, double
  * t + dt .. t + N_c dt.  psi_out/xi_out (a_out/b_out): host or device [N][R][2], caller-owned,
  * both or neither (NULL: the final state is not returned); they may be the input buffers.
  * Every time loop checks that U(dt) kept the norm of psi (a): KG_ENUMERIC when it drifts by
- * more than 1e-10 (FP64) or 1e-3 (KG_C64) relative, e.g. for a far too loose bessel_tol. */
+ * more than 1e-10 (FP64) or 1e-3 (KG_C64) relative, e.g. for a far too loose bessel_tol.
+ * The time loops (kg_vac, kg_msd and these) run the norm check, the non-finite check and the
+ * copy of the moments behind one stream synchronisation; on KG_ENUMERIC mu_out holds the
+ * offending moments. */
 kg_status kg_msd_resume(kg_hamiltonian* h, const kg_run* run, const double* psi, const double* xi,
                         double* mu_out, double* psi_out, double* xi_out);
 kg_status kg_vac_resume(kg_hamiltonian* h, const kg_run* run, const double* a, const double* b,

@@ -70,6 +70,9 @@ struct kg_hamiltonian {
     static constexpr int kNumVec = 10;
     kg::DevBuf vec[kNumVec];
     kg::DevBuf part_first, part_ring, moments, flag, norms, norm_part;
+    // pinned host staging for the end-of-run checks (non-finite flag and the norms)
+    void* host_stage = nullptr;
+    size_t host_stage_bytes = 0;
     // timing
     bool timing = false;
     std::vector<kg::TimedPhase> phases;
@@ -466,13 +469,36 @@ static kg_status block_norms(kg_hamiltonian* h, int R, const vec2_t<T>* x, int s
     return KG_OK;
 }
 
-// U(dt) is unitary (Eq. 36): the norm of the evolved vector must not drift.  Fails with
-// KG_ENUMERIC when any of the `slots` recorded norms differs from slot 0 by more than
+// U(dt) is unitary (Eq. 36): the norm of the evolved vector must not drift.  finish_run
+// fails with KG_ENUMERIC when any of the recorded norms differs from slot 0 by more than
 // 1e-10 (FP64) or 1e-3 (complex64) relative, e.g. for a Bessel truncation far too loose.
+// End of a time loop with one synchronisation: the non-finite check of the moments, the
+// copy of the norm record and of the flag into pinned host memory, and the copy of the
+// moments to the caller's buffer are all queued, then the stream is synchronised once and
+// the unitarity and finiteness conditions are evaluated (KG_ENUMERIC, as check_finite does
+// for the other entry points; the caller's buffer then holds the offending moments).
 template <typename T>
-static kg_status check_norms(kg_hamiltonian* h, int R, int slots) {
-    std::vector<double2> nrm((size_t)slots * R);
-    KG_CUDA_TRY(cudaMemcpyAsync(nrm.data(), h->norms.p, nrm.size() * sizeof(double2), cudaMemcpyDeviceToHost,
+static kg_status finish_run(kg_hamiltonian* h, int R, int slots, double* mu_out, size_t n_doubles) {
+    const size_t want = 64 + (size_t)slots * R * sizeof(double2);
+    if (h->host_stage_bytes < want) {
+        if (h->host_stage) cudaFreeHost(h->host_stage);
+        h->host_stage = nullptr;
+        h->host_stage_bytes = 0;
+        KG_CUDA_TRY(cudaMallocHost(&h->host_stage, want));
+        h->host_stage_bytes = want;
+    }
+    int* bad = (int*)h->host_stage;
+    double2* nrm = (double2*)((char*)h->host_stage + 64);
+    KG_TRY(h->flag.ensure(sizeof(int), h->stream));
+    KG_CUDA_TRY(cudaMemsetAsync(h->flag.p, 0, sizeof(int), h->stream));
+    KG_CUDA_TRY(launch_nonfinite((const double*)h->moments.p, (int64_t)n_doubles, (int*)h->flag.p, h->stream));
+    h->counters.other_launches += 1;
+    KG_CUDA_TRY(cudaMemcpyAsync(bad, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    if (slots > 0)
+        KG_CUDA_TRY(cudaMemcpyAsync(nrm, h->norms.p, (size_t)slots * R * sizeof(double2), cudaMemcpyDeviceToHost,
+                                    h->stream));
+    KG_CUDA_TRY(cudaMemcpyAsync(mu_out, h->moments.p, n_doubles * sizeof(double),
+                                is_device_ptr(mu_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                 h->stream));
     KG_CUDA_TRY(cudaStreamSynchronize(h->stream));
     const double tol = sizeof(T) == sizeof(double) ? 1e-10 : 1e-3;
@@ -486,6 +512,9 @@ static kg_status check_norms(kg_hamiltonian* h, int R, int slots) {
                                              std::to_string(t) + " steps (U(dt) must be unitary; bessel_tol?)");
         }
     }
+    if (*bad)
+        return fail(KG_ENUMERIC, "non-finite moments: the input vectors hold NaN/Inf entries or FP64 entries "
+                                 "of magnitude 2^63 or more");
     return KG_OK;
 }
 
@@ -511,7 +540,7 @@ static kg_status state_out(kg_hamiltonian* h, int R, const vec2_t<T>* src, int t
 // steps, with the moments after each step; the final state goes to (a_out, b_out) if given.
 template <typename T>
 static kg_status vac_impl(kg_hamiltonian* h, int R, int M, int NC, const Series& ser, const double* a_in,
-                          const double* b_in, bool resume, double* a_out, double* b_out) {
+                          const double* b_in, bool resume, double* a_out, double* b_out, double* mu_out) {
     using V2 = vec2_t<T>;
     // blocks: 0 A, 1 B, 2 A', 3 B', 4 L, 5 p1(A), 6 p1(B), 7 kpm b0, 8 kpm b1
     KG_TRY(ensure_vectors(h, R, 9));
@@ -545,10 +574,9 @@ static kg_status vac_impl(kg_hamiltonian* h, int R, int M, int NC, const Series&
         KG_TRY(kpm_moments<T>(h, R, M, false, L, B, VT<T>(h, 7), VT<T>(h, 8), mu + (int64_t)t * M,
                               (int64_t)NC * M));
     }
-    KG_TRY(check_norms<T>(h, R, slot + 1));
     if (a_out) KG_TRY(state_out<T>(h, R, A, 7, a_out));
     if (b_out) KG_TRY(state_out<T>(h, R, B, 8, b_out));
-    return KG_OK;
+    return finish_run<T>(h, R, slot + 1, mu_out, (size_t)R * NC * M * 2);
 }
 
 // MSD time loop (Algorithm 3, Eq. 44) on the state (psi, xi), psi = U(t) phi,
@@ -557,7 +585,7 @@ static kg_status vac_impl(kg_hamiltonian* h, int R, int M, int NC, const Series&
 // moments after each step; the final state goes to (psi_out, xi_out) if given.
 template <typename T>
 static kg_status msd_impl(kg_hamiltonian* h, int R, int M, int NC, const Series& ser, const double* psi_in,
-                          const double* xi_in, bool resume, double* psi_out, double* xi_out) {
+                          const double* xi_in, bool resume, double* psi_out, double* xi_out, double* mu_out) {
     using V2 = vec2_t<T>;
     // blocks: 0 psi, 1 xi, 2 psi', 3 xi', 4 p1(xi), 5 p1(psi), 6 q1, 7 q0
     KG_TRY(ensure_vectors(h, R, 8));
@@ -584,10 +612,9 @@ static kg_status msd_impl(kg_hamiltonian* h, int R, int M, int NC, const Series&
         KG_TRY(kpm_moments<T>(h, R, M, true, xi, xi, VT<T>(h, 4), VT<T>(h, 5), mu + (int64_t)t * M,
                               (int64_t)NC * M));
     }
-    KG_TRY(check_norms<T>(h, R, NC - t0 + 1));
     if (psi_out) KG_TRY(state_out<T>(h, R, psi, 6, psi_out));
     if (xi_out) KG_TRY(state_out<T>(h, R, xi, 7, xi_out));
-    return KG_OK;
+    return finish_run<T>(h, R, NC - t0 + 1, mu_out, (size_t)R * NC * M * 2);
 }
 
 static kg_status check_run(const kg_hamiltonian* h, const kg_run* run, bool need_time) {
@@ -703,6 +730,8 @@ void kg_destroy_hamiltonian(kg_hamiltonian* h) {
     if (!h) return;
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
+    if (h->host_stage) cudaFreeHost(h->host_stage);
+    h->host_stage = nullptr;
     h->idx.release();
     h->onsite.release();
     h->parity.release();
@@ -743,10 +772,8 @@ kg_status kg_vac(kg_hamiltonian* h, const kg_run* run, const double* phi, double
     Series ser;
     if (NC > 1) KG_TRY(series_for(h, run->dt, run->bessel_tol, &ser));
     KG_TRY(ensure_moments(h, (size_t)R * NC * M));
-    if (run->precision == KG_C64) KG_TRY(vac_impl<float>(h, R, M, NC, ser, phi, nullptr, false, nullptr, nullptr));
-    else KG_TRY(vac_impl<double>(h, R, M, NC, ser, phi, nullptr, false, nullptr, nullptr));
-    KG_TRY(check_finite(h, h->moments.p, (size_t)R * NC * M * 2));
-    return copy_out(h, h->moments.p, mu_out, (size_t)R * NC * M * sizeof(double2));
+    if (run->precision == KG_C64) return vac_impl<float>(h, R, M, NC, ser, phi, nullptr, false, nullptr, nullptr, mu_out);
+    return vac_impl<double>(h, R, M, NC, ser, phi, nullptr, false, nullptr, nullptr, mu_out);
 }
 
 kg_status kg_msd(kg_hamiltonian* h, const kg_run* run, const double* phi, double* mu_out) {
@@ -758,10 +785,8 @@ kg_status kg_msd(kg_hamiltonian* h, const kg_run* run, const double* phi, double
     Series ser;
     if (NC > 1) KG_TRY(series_for(h, run->dt, run->bessel_tol, &ser));
     KG_TRY(ensure_moments(h, (size_t)R * NC * M));
-    if (run->precision == KG_C64) KG_TRY(msd_impl<float>(h, R, M, NC, ser, phi, nullptr, false, nullptr, nullptr));
-    else KG_TRY(msd_impl<double>(h, R, M, NC, ser, phi, nullptr, false, nullptr, nullptr));
-    KG_TRY(check_finite(h, h->moments.p, (size_t)R * NC * M * 2));
-    return copy_out(h, h->moments.p, mu_out, (size_t)R * NC * M * sizeof(double2));
+    if (run->precision == KG_C64) return msd_impl<float>(h, R, M, NC, ser, phi, nullptr, false, nullptr, nullptr, mu_out);
+    return msd_impl<double>(h, R, M, NC, ser, phi, nullptr, false, nullptr, nullptr, mu_out);
 }
 
 kg_status kg_vac_resume(kg_hamiltonian* h, const kg_run* run, const double* a, const double* b, double* mu_out,
@@ -775,10 +800,8 @@ kg_status kg_vac_resume(kg_hamiltonian* h, const kg_run* run, const double* a, c
     Series ser;
     KG_TRY(series_for(h, run->dt, run->bessel_tol, &ser));
     KG_TRY(ensure_moments(h, (size_t)R * NC * M));
-    if (run->precision == KG_C64) KG_TRY(vac_impl<float>(h, R, M, NC, ser, a, b, true, a_out, b_out));
-    else KG_TRY(vac_impl<double>(h, R, M, NC, ser, a, b, true, a_out, b_out));
-    KG_TRY(check_finite(h, h->moments.p, (size_t)R * NC * M * 2));
-    return copy_out(h, h->moments.p, mu_out, (size_t)R * NC * M * sizeof(double2));
+    if (run->precision == KG_C64) return vac_impl<float>(h, R, M, NC, ser, a, b, true, a_out, b_out, mu_out);
+    return vac_impl<double>(h, R, M, NC, ser, a, b, true, a_out, b_out, mu_out);
 }
 
 kg_status kg_msd_resume(kg_hamiltonian* h, const kg_run* run, const double* psi, const double* xi, double* mu_out,
@@ -792,10 +815,8 @@ kg_status kg_msd_resume(kg_hamiltonian* h, const kg_run* run, const double* psi,
     Series ser;
     KG_TRY(series_for(h, run->dt, run->bessel_tol, &ser));
     KG_TRY(ensure_moments(h, (size_t)R * NC * M));
-    if (run->precision == KG_C64) KG_TRY(msd_impl<float>(h, R, M, NC, ser, psi, xi, true, psi_out, xi_out));
-    else KG_TRY(msd_impl<double>(h, R, M, NC, ser, psi, xi, true, psi_out, xi_out));
-    KG_TRY(check_finite(h, h->moments.p, (size_t)R * NC * M * 2));
-    return copy_out(h, h->moments.p, mu_out, (size_t)R * NC * M * sizeof(double2));
+    if (run->precision == KG_C64) return msd_impl<float>(h, R, M, NC, ser, psi, xi, true, psi_out, xi_out, mu_out);
+    return msd_impl<double>(h, R, M, NC, ser, psi, xi, true, psi_out, xi_out, mu_out);
 }
 
 kg_status kg_test_alloc_cap(uint64_t bytes) {
