@@ -693,14 +693,21 @@ kg_status kg_build_hamiltonian(const kg_lattice* lattice, const int64_t* vacanci
             h->dev.dh[p][k] = slot_displacement(hl.kind, lattice->bond_nm, p, k) * h->dev.h;
     h->dev.ytransport = (hl.kind == KG_AGNR);
     if (onsite_ev) {
-        std::vector<double> e((size_t)n + 1, 0.0);
-        for (int64_t k = 0; k < n; k++) e[(size_t)k] = hl.removed[(size_t)k] ? 0.0 : onsite_ev[k] / lattice->emax_ev;
+        // eps_n / E_max and, after it, 2 eps_n / E_max (exact): the recursion steps after the
+        // first read the doubled value instead of doubling it on the DP pipe
+        std::vector<double> e(2 * ((size_t)n + 1), 0.0);
+        for (int64_t k = 0; k < n; k++) {
+            e[(size_t)k] = hl.removed[(size_t)k] ? 0.0 : onsite_ev[k] / lattice->emax_ev;
+            e[(size_t)n + 1 + (size_t)k] = 2.0 * e[(size_t)k];
+        }
         st = h->onsite.ensure(e.size() * sizeof(double), h->stream);
         if (st != KG_OK) return bail(st);
         if (cudaMemcpyAsync(h->onsite.p, e.data(), e.size() * sizeof(double), cudaMemcpyHostToDevice,
                             h->stream) != cudaSuccess)
             return bail(fail(KG_ECUDA, "upload of on-site energies failed"));
+        KG_CUDA_TRY(cudaStreamSynchronize(h->stream));   // the host array goes out of scope
         h->dev.onsite = (const double*)h->onsite.p;
+        h->dev.onsite2 = (const double*)h->onsite.p + (n + 1);
     }
     if (h->dev.ytransport) {
         st = h->parity.ensure((size_t)n + 1, h->stream);

@@ -44,6 +44,7 @@ struct BatchArgs {
     const int32_t* idx;       // [3][n_total], sentinel = n_total
     int64_t n_total;
     const double* onsite;     // [n_total] scaled, or null
+    const double* onsite2;    // [n_total] the same doubled (steps after the first), or null
     const double* hop;        // [n_inst] -gamma0 / E_max,i
     const int* cta_inst;      // [n_cta]
     const int64_t* cta_s0;    // [n_cta] first site
@@ -132,7 +133,6 @@ __global__ void __launch_bounds__(kBThreads) batched_kpm_kernel(BatchArgs a) {
         const double2* cur = (n & 1) ? a.B : a.A;
         double2* out = (n & 1) ? a.A : a.B;   // in place over phi_{n-1} from n = 1 on
         const double c = n == 0 ? h : 2.0 * h;
-        const double ec = n == 0 ? 1.0 : 2.0;
         Dot64 acc0[kChunks], acc1[kChunks];
         // one thread covers kChunks vectors of a site, so the index loads are amortised over
         // them.  With one vector per thread (block width R) the next site's indices are
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kBThreads) batched_kpm_kernel(BatchArgs a) {
                 i2 = __ldg(a.idx + 2 * n_total + site);
             }
             double e = 0.0;
-            if constexpr (ONSITE) e = ec * __ldg(a.onsite + site);
+            if constexpr (ONSITE) e = n == 0 ? __ldg(a.onsite + site) : __ldg(a.onsite2 + site);
 #pragma unroll
             for (int q = 0; q < kChunks; q++) {
                 const int r = q * RB + rl;
@@ -299,6 +299,7 @@ struct Batch {
     void* mem = nullptr;
     int32_t* idx = nullptr;
     double* onsite_d = nullptr;
+    double* onsite2_d = nullptr;
     double* hop = nullptr;
     double2* A = nullptr;
     double2* B = nullptr;
@@ -467,14 +468,19 @@ static kg_status create_batch(kg_hamiltonian* const* hs, int n_h, int R, std::un
     const size_t b_hop = ((size_t)n_h * sizeof(double) + 255) & ~(size_t)255;
     const size_t b_vec = (((size_t)(total + 1) * R * sizeof(double2)) + 255) & ~(size_t)255;
     const size_t b_flags = 256 + (size_t)sm_count() * 64 * sizeof(int);
-    const size_t bytes = b_idx + b_on + b_hop + 2 * b_vec + b_flags;
+    const size_t bytes = b_idx + 2 * b_on + b_hop + 2 * b_vec + b_flags;
     if (cudaMalloc(&b->mem, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(KG_ENOMEM, "batched: device allocation failed");
     }
     char* p = (char*)b->mem;
     b->idx = (int32_t*)p; p += b_idx;
-    if (b->onsite) { b->onsite_d = (double*)p; p += b_on; }
+    if (b->onsite) {
+        b->onsite_d = (double*)p;
+        p += b_on;
+        b->onsite2_d = (double*)p;
+        p += b_on;
+    }
     b->hop = (double*)p; p += b_hop;
     b->A = (double2*)p; p += b_vec;
     b->B = (double2*)p; p += b_vec;
@@ -490,9 +496,16 @@ static kg_status create_batch(kg_hamiltonian* const* hs, int n_h, int R, std::un
         hop[i] = d.h;
         rebase_idx_kernel<<<stream_grid(3 * d.n), 256, 0, b->stream>>>(d.idx, d.n, b->offset[i], b->idx, total);
         KG_CUDA_TRY(cudaGetLastError());
-        if (d.onsite)
+        if (d.onsite) {
             KG_CUDA_TRY(cudaMemcpyAsync(b->onsite_d + b->offset[i], d.onsite, d.n * sizeof(double),
                                         cudaMemcpyDeviceToDevice, b->stream));
+            if (d.onsite2) {
+                KG_CUDA_TRY(cudaMemcpyAsync(b->onsite2_d + b->offset[i], d.onsite2, d.n * sizeof(double),
+                                            cudaMemcpyDeviceToDevice, b->stream));
+            } else {
+                return fail(KG_EINVAL, "batched: member without doubled on-site energies");
+            }
+        }
     }
     KG_CUDA_TRY(cudaMemcpyAsync(b->hop, hop.data(), n_h * sizeof(double), cudaMemcpyHostToDevice, b->stream));
     KG_CUDA_TRY(cudaStreamSynchronize(b->stream));
@@ -553,6 +566,7 @@ static kg_status run_graph(Batch* b, int cfg, int M) {
         a.idx = b->idx;
         a.n_total = b->n_total;
         a.onsite = b->onsite_d;
+        a.onsite2 = b->onsite2_d;
         a.hop = b->hop;
         a.cta_inst = s->cta_inst;
         a.cta_s0 = s->cta_s0;

@@ -65,6 +65,8 @@ struct DevH {
     int64_t istride = 0;
     int64_t n = 0;                  // sites; vectors have n + 1 rows (row n is zero)
     const double* onsite = nullptr; // eps_n / E_max, or null
+    const double* onsite2 = nullptr;// 2 eps_n / E_max (the factor of the steps after the first), or null
+                                    // (then formed from onsite)
     const uint8_t* parity = nullptr;// only for transport along y (AGNR)
     double h = 0.0;                 // H~ hopping  -gamma0 / E_max
     double dh[2][3] = {{0}};        // (X_n - X_m) * h per parity and slot (nm)

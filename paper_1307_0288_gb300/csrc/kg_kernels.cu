@@ -153,6 +153,14 @@ __device__ __forceinline__ void add_term(vec2_t<T>& a, bool odd, T cr, T ci, T y
     }
 }
 
+// On-site factor of a recursion step: eps_n / E_max on the first step, 2 eps_n / E_max on the
+// later ones (read pre-doubled when the Hamiltonian carries it: no DP multiply per item).
+template <bool FIRST>
+__device__ __forceinline__ double onsite_factor(const DevH& H, int64_t n) {
+    if (FIRST) return __ldg(H.onsite + n);
+    return H.onsite2 ? __ldg(H.onsite2 + n) : 2.0 * __ldg(H.onsite + n);
+}
+
 template <typename T>
 __device__ __forceinline__ vec2_t<T> mk(T x, T y);
 template <>
@@ -204,7 +212,7 @@ __global__ void __launch_bounds__(kBlock<T>) kpm_sym_kernel(DevH H, const vec2_t
         const int64_t n = w / R;
         const Nbr<T> g = gather_at<T, R>(nid, n, r, cur);
         T e = 0;
-        if constexpr (ONSITE) e = (T)((FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n));
+        if constexpr (ONSITE) e = (T)onsite_factor<FIRST>(H, n);
         vec2_t<T> z = mk<T>(0, 0);
         if constexpr (!FIRST) z = prev[w];
         if (w + stride < n_items) nid = load_idx(H.idx, H.istride, (w + stride) / R);
@@ -246,7 +254,7 @@ __global__ void __launch_bounds__(kBlock<T>) kpm_gen_kernel(DevH H, const vec2_t
         const int64_t n = w / R;
         const Nbr<T> g = gather_at<T, R>(nid, n, r, cur);
         T e = 0;
-        if constexpr (ONSITE) e = (T)((FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n));
+        if constexpr (ONSITE) e = (T)onsite_factor<FIRST>(H, n);
         vec2_t<T> z = mk<T>(0, 0);
         if constexpr (!FIRST) z = prev[w];
         const vec2_t<T> l = __ldg(L + w);
@@ -299,6 +307,9 @@ __global__ void __launch_bounds__(kBlock<T>) kpm_gen_kernel(DevH H, const vec2_t
 __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
+// The two halves of the cluster barrier, for work between them that peers do not read.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t map_cluster_rank(uint32_t local_smem, uint32_t rank) {
     uint32_t a;
@@ -404,6 +415,9 @@ __global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T
         const T yr = hop<T>(c, ga.x, gb.x, gc.x, e, x.x, z.x, ONSITE);
         const T yi = hop<T>(c, ga.y, gb.y, gc.y, e, x.y, z.y, ONSITE);
         if (valid) prvb[t] = mk<T>(yr, yi);
+        // phi_{n+1} is written: release it to the peers now, and form this step's inner
+        // products (registers and this CTA's own table only) while the barrier completes
+        cluster_arrive();
         Acc<T> a0, a1;   // padding threads hold zeros and add nothing
         if constexpr (SYM) {
             a0.add_prod(x.x, x.x);
@@ -444,7 +458,7 @@ __global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T
                 if (lane < R) wp[((int64_t)nsteps * nwarps + warp) * R + lane] = make_float4(u0, v0, u1, v1);
             }
         }
-        cluster_barrier();
+        cluster_wait();   // every peer's phi_{n+1} is visible before the next step's gathers
         cb ^= 1;
     }
     // no peer reads this CTA's buffers any more; write phi_n and phi_{n-1} back
@@ -452,6 +466,7 @@ __global__ void __launch_bounds__(512) kpm_cluster_kernel(DevH H, const vec2_t<T
         dst_cur[w] = sv[cb * (nt + 1) + t];
         dst_prev[w] = sv[(cb ^ 1) * (nt + 1) + t];
     }
+    __syncthreads();   // the last step's per-warp sums (written after its arrive) are in wp
     // cross-warp sums per (step, vector, product), fixed order, into ring slab k
     const int nslab = nsteps + ((!SYM && first) ? 1 : 0);
     for (int i = t; i < nslab * R * 2; i += nt) {
@@ -713,7 +728,7 @@ __global__ void __launch_bounds__(kThreads) kpm_sym_pair_kernel(DevH H, const fl
         const int64_t n = w / R2;
         const Nbr4 g = gather_pair<R2>(nid, n, r2, cur);
         float e = 0.0f;
-        if constexpr (ONSITE) e = (float)((FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n));
+        if constexpr (ONSITE) e = (float)onsite_factor<FIRST>(H, n);
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         if constexpr (!FIRST) z = prev[w];
         if (w + stride < n_items) nid = load_idx(H.idx, H.istride, (w + stride) / R2);
@@ -757,7 +772,7 @@ __global__ void __launch_bounds__(kThreads) kpm_gen_pair_kernel(DevH H, const fl
         const int64_t n = w / R2;
         const Nbr4 g = gather_pair<R2>(nid, n, r2, cur);
         float e = 0.0f;
-        if constexpr (ONSITE) e = (float)((FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n));
+        if constexpr (ONSITE) e = (float)onsite_factor<FIRST>(H, n);
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         if constexpr (!FIRST) z = prev[w];
         const float4 l = __ldg(L + w);
@@ -907,7 +922,7 @@ __global__ void __launch_bounds__(kBlock<T>) evolve_kernel(DevH H, double j0d, d
         const Idx3 id = nid;
         if (w + stride < n_items) nid = load_idx(H.idx, H.istride, (w + stride) / R);
         T e = 0;
-        if constexpr (ONSITE) e = (T)((FIRST ? 1.0 : 2.0) * __ldg(H.onsite + n));
+        if constexpr (ONSITE) e = (T)onsite_factor<FIRST>(H, n);
         V2 q_add = mk<T>(0, 0);   // chain-0 accumulator, finished after the commutator chain
         Nbr<T> gs;
 #pragma unroll
