@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <unordered_map>
 
 #include "kg_dot.cuh"
@@ -1100,11 +1101,26 @@ static int one_wave_grid(K kernel, int64_t n_items, int threads = kThreads) {
     if (it != cache.end()) {
         per_sm = it->second;
     } else {
-        // the grid-stride kernels keep at most a few KB in shared memory: give the rest of
-        // the unified L1/shared storage to L1, which serves the in-chain neighbour gathers
+        // The grid-stride kernels keep at most a few KB in shared memory: give the rest of the
+        // unified L1/shared storage to L1, which serves the in-chain neighbour gathers, but no
+        // less shared memory than the CTAs that the registers allow need (static table + the
+        // 1 KB the system reserves per CTA), so the carve-out never caps the occupancy.
+        int by_regs = 0;
+        cudaFuncAttributes fa{};
+        int dev = 0, smem_sm = 0;
         if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxL1) != cudaSuccess)
+                                 (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&by_regs, kernel, threads, 0) == cudaSuccess &&
+            cudaFuncGetAttributes(&fa, kernel) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+            smem_sm > 0) {
+            const double need = (double)by_regs * ((double)fa.sharedSizeBytes + 1024.0);
+            const int pct = std::min(100, std::max(0, (int)std::ceil(100.0 * need / smem_sm)));
+            if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess)
+                cudaGetLastError();
+        } else {
             cudaGetLastError();
+        }
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
             per_sm < 1) {
             cudaGetLastError();
