@@ -241,3 +241,11 @@ def test_jackknife_error_of_sigma_sc_plateau():
     assert se_avg > 0
     assert abs(se_avg - single.std(ddof=1) / np.sqrt(n)) < 1e-9 * max(1.0, se_avg)
     assert abs(ja - single.mean()) < 1e-9 * max(1.0, abs(ja))
+
+
+def test_fp64_fma_rate_rejects_bad_arguments():
+    """kg_fp64_fma_rate validates its arguments before touching a GPU."""
+    for bad in (0, 101, -3):
+        with pytest.raises(kg.KgError) as e:
+            kg.fp64_fma_rate(bad)
+        assert e.value.status == -1

@@ -353,3 +353,13 @@ def test_clean_zgnr_einstein_conductance_is_quantised():
     _, g = kg.ballistic(rho, rdx, dt_fs, width)
     assert np.allclose(g[2, :3], 2.0, rtol=0.05), g[2]
     assert np.all(g[2, 3:] > 6.0 * 0.97) and np.all(g[2, 3:] < 6.0 * 1.6), g[2]
+
+
+def test_fp64_fma_rate_probe_is_plausible():
+    """The in-library FP64 FMA probe (the benchmark's roofline denominator) reports a rate
+    within a factor of two of the GB300's nominal 0.625e12 FMA/s (1.25 TFLOP/s), and
+    the best of several launches is stable to a few per cent."""
+    a = kg.fp64_fma_rate(5)
+    b = kg.fp64_fma_rate(5)
+    assert 0.3e12 < a < 1.3e12, a
+    assert abs(a - b) / max(a, b) < 0.05, (a, b)
