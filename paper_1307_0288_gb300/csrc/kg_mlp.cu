@@ -436,30 +436,43 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // The whole network for batch inference in one persistent kernel, so activations never
 // leave the SM.  A CTA takes 128-row tiles in pairs (X, Y).  Shared memory holds the two
 // tiles' BF16 activations (2 x 64 KB, the canonical K-major no-swizzle layout of the
-// tiled format) and a ring of three 32 KB weight blocks (64 K values of one 256 x 256
-// layer); TMEM holds one 128 x 256 FP32 accumulator per tile (all 512 columns).
-//   warps 0-15  layer 1 (3 -> 256, CUDA cores) straight into the tile buffer, then every
-//               epilogue: GELU from TMEM back into the tile buffer as the next layer's
-//               operand, and the next layer's bias stored into the accumulator (tcgen05.st)
-//               for its MMAs to accumulate onto; after layer 4 the fused 256 -> 1 output.
-//               Warp w reads TMEM lanes 32 (w % 4) .. + 31 (the rule for tcgen05.ld) and
-//               64 columns; four warps per scheduler hide the TMEM, SFU and shared latencies;
-//   warp 16     streams the weight blocks with cp.async.bulk (from L2 after the first tiles),
-//               in the order the MMAs use them: per layer X's four blocks, then Y's;
+// tiled format), a ring of three 32 KB weight blocks (64 K values of one 256 x 256 layer)
+// and a 128 x 8 block of ones; TMEM holds one 128 x 256 FP32 accumulator per tile (all
+// 512 columns).  Every layer, bias included, runs on the tensor cores:
+//   layer 1   one K = 16 MMA: the tile's rows [xh, xt, xh, xt, 1, 1, 1, 0] (x = xh + xt in
+//             BF16, written into the tile's first two k-chunks) against the block
+//             [Wh, Wh, Wt, Wt, bh, bt, bu, 0] (W1 = Wh + Wt, b1 = bh + bt + bu), i.e.
+//             W1 x + b1 to about 2^-16 relative;
+//   layers 2-4  one K = 16 MMA of the ones block against [bh, bt, bu, 0, ...] (the bias,
+//             exact in FP32) starts the accumulator, then 16 MMAs over the layer's four
+//             K blocks accumulate W a onto it.
+//   warps 0-15  write the layer-1 rows (column groups 0 and 1, inputs loaded a pair ahead)
+//               and run every epilogue: GELU from TMEM back into the tile buffer as the next
+//               layer's operand; after layer 4 the fused 256 -> 1 output.  Warp w reads TMEM
+//               lanes 32 (w % 4) .. + 31 (the rule for tcgen05.ld) and 64 columns; four warps
+//               per scheduler hide the TMEM, SFU and shared latencies;
+//   warp 16     streams the blocks with cp.async.bulk (from L2 after the first tiles), in the
+//               order the MMAs use them: per pair the layer-1 block (read by both tiles), then
+//               per layer X's bias block and four weight blocks, then Y's;
 //   warp 17     issues the tcgen05 MMAs and owns the TMEM.
-// Per pair the order is L1(X) L1(Y) | M2(X) M2(Y) M3(X) M3(Y) M4(X) M4(Y), and the epilogue
+// Per pair the order is M1(X) M1(Y) | M2(X) M2(Y) M3(X) M3(Y) M4(X) M4(Y), and the epilogue
 // of one tile overlaps the other tile's MMAs.  Every wait is bounded.
 constexpr int kFSlots = 3;
 constexpr int kFWAtom = BN * BK * 2;                     // 32 KB: 8 k-chunks x 256 rows x 16 B
+constexpr int kFXAtom = BN * 16 * 2;                     // 8 KB: a K = 16 block, 2 k-chunks x 256 rows x 16 B
 constexpr int kFTile = BM * H * 2;                       // 64 KB
-constexpr int kFSmem = 2 * kFTile + kFSlots * kFWAtom + 128 + 16 + 128;
+constexpr int kFOnes = BM * 16;                          // 2 KB: 128 rows x 8 BF16 ones
+// tiles, ring, barriers (128 B), TMEM address (padded to 128 B), ones, alignment slack
+constexpr int kFSmem = 2 * kFTile + kFSlots * kFWAtom + 128 + 128 + kFOnes + 128;
+static_assert(kFSmem <= 232448, "fused kernel shared memory");
 
 struct FArgs {
     const float* x;                  // [rows][3], rows >= n_valid read as zero
     int64_t n_valid;
     int64_t n_tiles;                 // 128-row tiles (pairs run past an odd count on zeros)
     const float* params;             // flat FP32 parameters (W1, b1, ..., w5, b5)
-    const __nv_bfloat16* w_tiled;    // [3][32][256][8] BF16 weights of layers 2..4
+    const __nv_bfloat16* w_tiled;    // [3][32][256][8] BF16 weights of layers 2..4 (halved)
+    const __nv_bfloat16* w_extra;    // [4][2][256][8] K = 16 blocks: layer 1, biases of layers 2..4
     float* y;                        // [n_valid]
     int* error;
 };
@@ -475,6 +488,7 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
     const uint32_t w_full = bars, w_empty = bars + 8 * kFSlots, a_ready = bars + 16 * kFSlots,
                    acc_full = bars + 16 * kFSlots + 16;
     uint32_t* tmem_slot = (uint32_t*)(base_ptr + 2 * kFTile + kFSlots * kFWAtom + 128);
+    const uint32_t sOnes = bars + 256;
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n_pairs = (p.n_tiles + 1) / 2;
@@ -490,6 +504,12 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
             mbar_init(acc_full + 8 * t, 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp < 4) {
+        // the ones block (BF16 1.0 = 0x3F80), one 16-byte core-matrix row per thread; the first
+        // publish of every compute warp fences it for the tensor cores
+        const uint32_t one2 = 0x3F803F80u;
+        st_shared_v4(sOnes + (uint32_t)tid * 16, make_uint4(one2, one2, one2, one2));
     }
     if (warp == kFCW + 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -507,22 +527,31 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
     };
 
     if (warp == kFCW && lane == 0) {
-        // weight blocks in MMA order: per pair, per layer, per tile, four K blocks
+        // blocks in MMA order: per pair the layer-1 block, then per layer and tile the bias
+        // block and four weight K blocks
         int64_t g = 0;
-        for (int64_t pr = blockIdx.x; pr < n_pairs && !s_abort; pr += gridDim.x) {
-            for (int l = 0; l < 3 && !s_abort; l++)
-                for (int t = 0; t < 2 && !s_abort; t++)
-                    for (int k = 0; k < 4; k++, g++) {
-                        const int slot = (int)(g % kFSlots);
-                        const int64_t use = g / kFSlots;
-                        if (use > 0 && !pwait(w_empty + 8 * slot, (uint32_t)((use - 1) & 1), &s_abort)) {
-                            give_up();
-                            break;
-                        }
-                        expect_tx(w_full + 8 * slot, kFWAtom);
-                        bulk_g2s(sW + slot * kFWAtom, (const uint8_t*)p.w_tiled + ((size_t)l * 4 + k) * kFWAtom,
-                                 kFWAtom, w_full + 8 * slot);
-                    }
+        auto fill = [&](const void* src, uint32_t bytes) -> bool {
+            const int slot = (int)(g % kFSlots);
+            const int64_t use = g / kFSlots;
+            if (use > 0 && !pwait(w_empty + 8 * slot, (uint32_t)((use - 1) & 1), &s_abort)) {
+                give_up();
+                return false;
+            }
+            expect_tx(w_full + 8 * slot, bytes);
+            bulk_g2s(sW + slot * kFWAtom, src, bytes, w_full + 8 * slot);
+            g++;
+            return true;
+        };
+        const uint8_t* extra = (const uint8_t*)p.w_extra;
+        bool ok = true;
+        for (int64_t pr = blockIdx.x; pr < n_pairs && ok && !s_abort; pr += gridDim.x) {
+            ok = fill(extra, kFXAtom);
+            for (int l = 0; l < 3 && ok; l++)
+                for (int t = 0; t < 2 && ok; t++) {
+                    ok = fill(extra + (size_t)(l + 1) * kFXAtom, kFXAtom);
+                    for (int k = 0; k < 4 && ok; k++)
+                        ok = fill((const uint8_t*)p.w_tiled + ((size_t)l * 4 + k) * kFWAtom, kFWAtom);
+                }
         }
         // no copy may still be landing when the CTA exits (bounded, ignores the abort flag)
         volatile int never = 0;
@@ -531,50 +560,79 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
     } else if (warp == kFCW + 1 && lane == 0) {
         int64_t g = 0, job[2] = {0, 0};
         uint32_t last_bar = 0, last_parity = 0;
-        for (int64_t pr = blockIdx.x; pr < n_pairs && !s_abort; pr += gridDim.x) {
-            for (int l = 0; l < 3 && !s_abort; l++)
-                for (int t = 0; t < 2 && !s_abort; t++) {
-                    const int64_t jt = job[t]++;   // job index of tile t: a_ready / acc_full phase
-                    // the tile's operand for this layer is written and its accumulator drained
-                    if (!pwait(a_ready + 8 * t, (uint32_t)(jt & 1), &s_abort)) {
-                        give_up();
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    bool ok = true;
-                    for (int k = 0; k < 4; k++, g++) {
-                        const int slot = (int)(g % kFSlots);
-                        if (!pwait(w_full + 8 * slot, (uint32_t)((g / kFSlots) & 1), &s_abort)) {
-                            give_up();
-                            ok = false;
-                            break;
-                        }
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        auto mma = [&](int t, uint64_t ad, uint64_t bd, uint32_t accum) {
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * BN),
+                "l"(ad), "l"(bd), "r"(kIdesc), "r"(accum)
+                : "memory");
+        };
+        auto commit = [&](uint32_t bar, uint32_t parity) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                         : "memory");
+            last_bar = bar;
+            last_parity = parity;
+        };
+        // the block of ring use g has landed
+        auto block_ready = [&]() -> bool {
+            if (!pwait(w_full + 8 * (int)(g % kFSlots), (uint32_t)((g / kFSlots) & 1), &s_abort)) {
+                give_up();
+                return false;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            return true;
+        };
+        // the tile's operand for its next layer is written and its accumulator drained
+        auto operand_ready = [&](int t) -> bool {
+            if (!pwait(a_ready + 8 * t, (uint32_t)(job[t] & 1), &s_abort)) {
+                give_up();
+                return false;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            return true;
+        };
+        // K = 16 descriptors: A = two k-chunks of a tile (LBO = 128 rows x 16 B) or the ones block
+        // read twice (LBO = 0); B = two k-chunks of the 256-row block in a ring slot
+        const uint64_t ones_desc = ns_desc(sOnes, 0, 128);
+        bool ok = true;
+        for (int64_t pr = blockIdx.x; pr < n_pairs && ok && !s_abort; pr += gridDim.x) {
+            // layer 1: both tiles read the one layer-1 block
+            ok = block_ready();
+            const uint32_t slot1 = sW + (uint32_t)(g % kFSlots) * kFWAtom;
+            for (int t = 0; t < 2 && ok; t++) {
+                ok = operand_ready(t);
+                if (!ok) break;
+                mma(t, ns_desc(sA + t * kFTile, BM * 16, 128), ns_desc(slot1, BN * 16, 128), 0u);
+                commit(acc_full + 8 * t, (uint32_t)(job[t] & 1));
+                job[t]++;
+            }
+            if (!ok) break;
+            commit(w_empty + 8 * (int)(g % kFSlots), (uint32_t)((g / kFSlots) & 1));
+            g++;
+            for (int l = 0; l < 3 && ok; l++)
+                for (int t = 0; t < 2 && ok; t++) {
+                    ok = operand_ready(t);
+                    // the bias: ones x [bh, bt, bu, 0, ...] starts the accumulator
+                    ok = ok && block_ready();
+                    if (!ok) break;
+                    mma(t, ones_desc, ns_desc(sW + (uint32_t)(g % kFSlots) * kFWAtom, BN * 16, 128), 0u);
+                    commit(w_empty + 8 * (int)(g % kFSlots), (uint32_t)((g / kFSlots) & 1));
+                    g++;
+                    for (int k = 0; k < 4 && ok; k++) {
+                        ok = block_ready();
+                        if (!ok) break;
+                        const uint32_t slot = sW + (uint32_t)(g % kFSlots) * kFWAtom;
 #pragma unroll
-                        for (int st = 0; st < BK / 16; st++) {
-                            // A: k-chunks 8k + 2st, +1 of the tile (LBO = 128 rows x 16 B, SBO = 8 rows x 16 B)
-                            const uint64_t ad = ns_desc(sA + t * kFTile + (k * 8 + 2 * st) * BM * 16, BM * 16, 128);
-                            // B: k-chunks 2st, +1 of the 256-row weight block in the slot
-                            const uint64_t bd = ns_desc(sW + slot * kFWAtom + 2 * st * BN * 16, BN * 16, 128);
-                            const uint32_t accum = 1u;   // on top of the bias the epilogue preloaded
-                            asm volatile(
-                                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * BN),
-                                "l"(ad), "l"(bd), "r"(kIdesc), "r"(accum)
-                                : "memory");
-                        }
-                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                         w_empty + 8 * slot)
-                                     : "memory");
-                        last_bar = w_empty + 8 * slot;
-                        last_parity = (uint32_t)((g / kFSlots) & 1);
+                        for (int st = 0; st < BK / 16; st++)
+                            // A: k-chunks 8k + 2st, +1 of the tile; B: k-chunks 2st, +1 of the block
+                            mma(t, ns_desc(sA + t * kFTile + (k * 8 + 2 * st) * BM * 16, BM * 16, 128),
+                                ns_desc(slot + 2 * st * BN * 16, BN * 16, 128), 1u);
+                        commit(w_empty + 8 * (int)(g % kFSlots), (uint32_t)((g / kFSlots) & 1));
+                        g++;
                     }
                     if (!ok) break;
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     acc_full + 8 * t)
-                                 : "memory");
-                    last_bar = acc_full + 8 * t;
-                    last_parity = (uint32_t)(jt & 1);
+                    commit(acc_full + 8 * t, (uint32_t)(job[t] & 1));
+                    job[t]++;
                 }
         }
         // every MMA issued must be complete before the TMEM is freed (bounded)
@@ -584,100 +642,62 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
         // warp w: TMEM lanes (tile rows) 32 (w % 4) .. + 31, accumulator columns of group w / 4
         const int quarter = warp & 3, grp = warp >> 2;
         const int rl = quarter * 32 + lane;
-        const float* W1 = p.params + kOffW1;
-        const float* b1 = p.params + kOffB1;
         const float* w5 = p.params + kOffW5;
         const float b5 = __ldg(p.params + kOffB5);
         int64_t job[2] = {0, 0};
-        // The accumulator of a tile starts each layer holding that layer's bias in every
-        // row, so the MMAs accumulate on top of it and the epilogue adds no bias.
-        auto preload_bias = [&](int t, int layer) {
-            const float4* bias4 = (const float4*)(p.params + layer_b(layer));
-#pragma unroll 1
-            for (int cb = 0; cb < kFCols / 32; cb++) {
-                const int col0 = grp * kFCols + cb * 32;
-                uint32_t v[32];
-#pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    const float4 b = __ldg(bias4 + col0 / 4 + q);
-                    v[4 * q] = __float_as_uint(b.x);
-                    v[4 * q + 1] = __float_as_uint(b.y);
-                    v[4 * q + 2] = __float_as_uint(b.z);
-                    v[4 * q + 3] = __float_as_uint(b.w);
-                }
-                KG_TMEM_ST32(tmem + t * BN + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0, v);
-            }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        };
-        // all compute warps have written the tile's operand and the accumulator's bias: publish
+        // all compute warps have written the tile's operand: publish
+        // (and its reads of the tile's accumulator are complete: the next MMA overwrites it)
         auto publish = [&](int t) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(a_ready + 8 * t);
         };
-        for (int64_t pr = blockIdx.x; pr < n_pairs; pr += gridDim.x) {
-            // layer 1: warp w covers k-chunks 2w, 2w + 1 (16 columns), lane covers rows
-            // lane + 32 i; the column weights are warp-uniform 16-byte loads
+        // the inputs of row rl of both tiles of a pair (column groups 0 and 1 write the layer-1
+        // rows); the next pair's are loaded while this pair runs
+        float xin[2][3];
+        auto load_x = [&](int64_t pr) {
+#pragma unroll
             for (int t = 0; t < 2; t++) {
-                const int64_t row0 = (2 * pr + t) * BM;
-                float xr[4][3];
+                const int64_t grow = (2 * pr + t) * BM + rl;
+                const bool in = grp < 2 && pr < n_pairs && grow < p.n_valid;
 #pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const int64_t grow = row0 + lane + 32 * i;
-                    xr[i][0] = xr[i][1] = xr[i][2] = 0.f;
-                    if (grow < p.n_valid) {
-                        xr[i][0] = __ldg(p.x + grow * 3 + 0);
-                        xr[i][1] = __ldg(p.x + grow * 3 + 1);
-                        xr[i][2] = __ldg(p.x + grow * 3 + 2);
+                for (int i = 0; i < 3; i++) xin[t][i] = in ? __ldg(p.x + grow * 3 + i) : 0.0f;
+            }
+        };
+        load_x(blockIdx.x);
+        for (int64_t pr = blockIdx.x; pr < n_pairs; pr += gridDim.x) {
+            // layer-1 rows: k-chunk 0 = [xh0 xh1 xh2 xt0 xt1 xt2 xh0 xh1],
+            //               k-chunk 1 = [xh2 xt0 xt1 xt2 1 1 1 0]   (x = xh + xt in BF16)
+#pragma unroll
+            for (int t = 0; t < 2; t++) {
+                if (grp < 2) {
+                    __nv_bfloat16 xh[3], xt[3];
+#pragma unroll
+                    for (int i = 0; i < 3; i++) {
+                        xh[i] = __float2bfloat16_rn(xin[t][i]);
+                        xt[i] = __float2bfloat16_rn(xin[t][i] - __bfloat162float(xh[i]));
                     }
+                    auto pk = [](__nv_bfloat16 lo, __nv_bfloat16 hi) {
+                        return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+                    };
+                    const uint32_t one2 = 0x3F803F80u, one_zero = 0x00003F80u;
+                    const uint4 row = grp == 0 ? make_uint4(pk(xh[0], xh[1]), pk(xh[2], xt[0]), pk(xt[1], xt[2]), pk(xh[0], xh[1]))
+                                               : make_uint4(pk(xh[2], xt[0]), pk(xt[1], xt[2]), one2, one_zero);
+                    st_shared_v4(sA + t * kFTile + (uint32_t)((grp * BM + rl) * 16), row);
                 }
-#pragma unroll 1
-                for (int cq = 0; cq < 32 / kFCW; cq++) {
-                    const int ch = warp * (32 / kFCW) + cq;        // k-chunk: columns 8 ch .. 8 ch + 7
-                    float w[24], bb[8];
-                    const float4* w4 = (const float4*)(W1 + ch * 24);
-#pragma unroll
-                    for (int q = 0; q < 6; q++) {
-                        const float4 f = __ldg(w4 + q);
-                        w[4 * q] = f.x;
-                        w[4 * q + 1] = f.y;
-                        w[4 * q + 2] = f.z;
-                        w[4 * q + 3] = f.w;
-                    }
-                    const float4 bl = __ldg((const float4*)(b1 + ch * 8)), bh = __ldg((const float4*)(b1 + ch * 8 + 4));
-                    bb[0] = bl.x; bb[1] = bl.y; bb[2] = bl.z; bb[3] = bl.w;
-                    bb[4] = bh.x; bb[5] = bh.y; bb[6] = bh.z; bb[7] = bh.w;
-#pragma unroll
-                    for (int i = 0; i < 4; i++) {
-                        uint32_t packed[4];
-#pragma unroll
-                        for (int e = 0; e < 8; e += 2) {
-                            // columns e, e + 1 side by side: z = W1 x + b1 with packed FMAs
-                            uint64_t z = f2_pack(bb[e], bb[e + 1]);
-                            z = f2_fma(f2_pack(w[3 * e + 2], w[3 * e + 5]), f2_pack(xr[i][2], xr[i][2]), z);
-                            z = f2_fma(f2_pack(w[3 * e + 1], w[3 * e + 4]), f2_pack(xr[i][1], xr[i][1]), z);
-                            z = f2_fma(f2_pack(w[3 * e], w[3 * e + 3]), f2_pack(xr[i][0], xr[i][0]), z);
-                            const float2 g = f2_unpack(gelu2_twice(z));   // 2 GELU (W2 streamed halved)
-                            const __nv_bfloat162 b2 = __floats2bfloat162_rn(g.x, g.y);
-                            packed[e >> 1] = *(const uint32_t*)&b2;
-                        }
-                        st_shared_v4(sA + t * kFTile + (uint32_t)((ch * BM + lane + 32 * i) * 16),
-                                     make_uint4(packed[0], packed[1], packed[2], packed[3]));
-                    }
-                }
-                preload_bias(t, 2);
                 publish(t);
             }
-            // layers 2-4: epilogues.  After an abort every wait returns at once, but all compute
+            load_x(pr + gridDim.x);
+            // epilogues of layers 1-4.  After an abort every wait returns at once, but all compute
             // warps still run every iteration, so each reaches every named barrier below.
-            for (int l = 0; l < 3; l++)
+            for (int l = 0; l < 4; l++)
                 for (int t = 0; t < 2; t++) {
                     const bool ok = pwait(acc_full + 8 * t, (uint32_t)(job[t] & 1), &s_abort);
                     job[t]++;
                     if (!ok) {
                         give_up();
-                        if (l == 2) {
+                        if (l == 3) {
                             asm volatile("bar.sync 1, %0;" ::"n"(kFCW * 32) : "memory");
                             asm volatile("bar.sync 1, %0;" ::"n"(kFCW * 32) : "memory");
                         }
@@ -685,7 +705,7 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     // 16-column chunks; the next chunk's TMEM load is in flight while this one's
-                    // GELU runs.  The epilogue stores 2 GELU(z) (layers 3 and 4 stream W/2); the
+                    // GELU runs.  The epilogue stores 2 GELU(z) (layers 2-4 stream W/2); the
                     // output layer sums w5 . 2 GELU(z4) in four partial sums and halves the total.
                     float ys[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                     const uint32_t trow = tmem + t * BN + ((uint32_t)(quarter * 32) << 16);
@@ -699,7 +719,7 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                         uint32_t* v = (cb & 1) ? vb : va;
                         uint32_t* vn = (cb & 1) ? va : vb;
                         if (cb + 1 < kChunk16) KG_TMEM_LD16(trow + (uint32_t)(col0 + 16), vn);
-                        if (l == 2) {
+                        if (l == 3) {
                             const float4* w54 = (const float4*)(w5 + col0);
 #pragma unroll
                             for (int q = 0; q < 4; q++) {
@@ -727,15 +747,13 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                         if (cb + 1 < kChunk16) KG_TMEM_WAIT16(vn);
                     }
                     const float ysum = 0.5f * ((ys[0] + ys[1]) + (ys[2] + ys[3]));
-                    if (l < 2) {
-                        preload_bias(t, l + 3);
+                    if (l < 3) {
                         publish(t);
                     } else {
                         // accumulator read: the next pair's layer 1 may now be followed by MMAs.
                         // The column groups' partial sums meet in the tile's operand buffer,
                         // which the completed layer-4 MMAs no longer read; the second barrier
-                        // keeps the next pair's layer 1 from overwriting them before they are read.
-                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        // keeps the next pair's layer-1 rows from overwriting them before they are read.
                         float* ypart = (float*)(base_ptr + t * kFTile);   // [kFGroups][128]
                         ypart[grp * BM + rl] = ysum;
                         asm volatile("bar.sync 1, %0;" ::"n"(kFCW * 32) : "memory");
@@ -914,9 +932,40 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
     }
 }
 
-// BF16 copies of W2..W4 ([out][in]) and their transposes ([in][out]).
+// The i-th of three BF16 terms whose sum is v exactly (FP32 has 24 significand bits, BF16 8):
+// h = bf16(v), t = bf16(v - h), u = v - h - t (exact in BF16).
+__device__ __forceinline__ float bf16_term(float v, int i) {
+    const float h = __bfloat162float(__float2bfloat16_rn(v));
+    const float r = v - h;
+    const float t = __bfloat162float(__float2bfloat16_rn(r));
+    return i == 0 ? h : i == 1 ? t : r - t;
+}
+
+// BF16 copies of W2..W4 ([out][in]) and their transposes ([in][out]), and the blocks of the
+// fused inference kernel.
 __global__ void cast_weights_kernel(const float* __restrict__ p, __nv_bfloat16* __restrict__ w,
-                                    __nv_bfloat16* __restrict__ wt, __nv_bfloat16* __restrict__ wtile) {
+                                    __nv_bfloat16* __restrict__ wt, __nv_bfloat16* __restrict__ wtile,
+                                    __nv_bfloat16* __restrict__ wextra) {
+    // K = 16 blocks [4][2 k-chunks][256 rows][8], row = output unit o, k-th value of the row:
+    //   block 0 (layer 1): k 0-2 Wh, 3-5 Wh, 6-8 Wt, 9-11 Wt (W1 = Wh + Wt), 12-14 the three
+    //     terms of b1, 15 zero -- against the rows [xh, xt, xh, xt, 1, 1, 1, 0];
+    //   blocks 1-3 (biases of layers 2-4): k 0-2 the three terms of the bias, the rest zero --
+    //     against rows of ones.
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 4 * H * 16; k += gridDim.x * blockDim.x) {
+        const int blk = k / (H * 16), o = (k / 16) % H, kk = k % 16;
+        float v = 0.0f;
+        if (blk == 0) {
+            if (kk < 12) {
+                const float wv = p[kOffW1 + o * 3 + kk % 3];
+                v = kk < 6 ? bf16_term(wv, 0) : wv - bf16_term(wv, 0);
+            } else if (kk < 15) {
+                v = bf16_term(p[kOffB1 + o], kk - 12);
+            }
+        } else if (kk < 3) {
+            v = bf16_term(p[layer_b(blk + 1) + o], kk);
+        }
+        wextra[blk * H * 16 + ((kk >> 3) * H + o) * 8 + (kk & 7)] = __float2bfloat16_rn(v);
+    }
     const int64_t total = 3 * (int64_t)H * H;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(k / (H * H));
@@ -950,6 +999,7 @@ struct kg_mlp {
     __nv_bfloat16* w = nullptr;    // [3][H][H]
     __nv_bfloat16* wt = nullptr;   // [3][H][H]
     __nv_bfloat16* wtile = nullptr;   // [3][32][H][8] (tiled for the persistent kernel)
+    __nv_bfloat16* wextra = nullptr;  // [4][2][H][8] (its layer-1 and bias blocks)
     int* error = nullptr;
     double* loss = nullptr;
     int64_t step = 0;
@@ -1097,6 +1147,7 @@ kg_status mlp_infer(kg_mlp* m, int64_t n_valid, int64_t rows) {
     fa.n_tiles = rows / BM;
     fa.params = m->params;
     fa.w_tiled = m->wtile;
+    fa.w_extra = m->wextra;
     fa.y = m->y;
     fa.error = m->error;
     const int64_t n_pairs = (fa.n_tiles + 1) / 2;
@@ -1229,7 +1280,7 @@ kg_status kg_mlp_create(const float* params, void* cuda_stream, kg_mlp** out) {
     };
     const size_t pb = kParams * sizeof(float);
     void* p = nullptr;
-    if (cudaMalloc(&p, 4 * pb + 3 * 3 * H * H * sizeof(__nv_bfloat16) + 256) != cudaSuccess) {
+    if (cudaMalloc(&p, 4 * pb + (3 * 3 * H * H + 4 * 16 * H) * sizeof(__nv_bfloat16) + 256) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(KG_ENOMEM, "mlp: device allocation failed"));
     }
@@ -1241,6 +1292,7 @@ kg_status kg_mlp_create(const float* params, void* cuda_stream, kg_mlp** out) {
     m->w = (__nv_bfloat16*)(c + ((4 * pb + 255) & ~(size_t)255));
     m->wt = m->w + 3 * H * H;
     m->wtile = m->wt + 3 * H * H;
+    m->wextra = m->wtile + 3 * H * H;
     void* q = nullptr;
     if (cudaMalloc(&q, 256) != cudaSuccess) return bail(fail(KG_ENOMEM, "mlp: device allocation failed"));
     m->error = (int*)q;
@@ -1250,7 +1302,7 @@ kg_status kg_mlp_create(const float* params, void* cuda_stream, kg_mlp** out) {
     if (cudaMemcpyAsync(m->params, params, pb, is_dev(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                         m->stream) != cudaSuccess)
         return bail(fail(KG_ECUDA, "mlp: parameter upload failed"));
-    cast_weights_kernel<<<256, 256, 0, m->stream>>>(m->params, m->w, m->wt, m->wtile);
+    cast_weights_kernel<<<256, 256, 0, m->stream>>>(m->params, m->w, m->wt, m->wtile, m->wextra);
     if (cudaStreamSynchronize(m->stream) != cudaSuccess)
         return bail(fail(KG_ECUDA, std::string("mlp: ") + cudaGetErrorString(cudaGetLastError())));
     *out = m;
@@ -1312,7 +1364,7 @@ kg_status kg_mlp_train_step(kg_mlp* m, const float* x, const float* t, int64_t n
     adam_kernel<<<256, 256, 0, m->stream>>>(m->params, m->grad, m->adam_m, m->adam_v, kParams, lr, b1, b2, 1e-8f,
                                             c1, c2);
     KG_CUDA_TRY(cudaGetLastError());
-    cast_weights_kernel<<<256, 256, 0, m->stream>>>(m->params, m->w, m->wt, m->wtile);
+    cast_weights_kernel<<<256, 256, 0, m->stream>>>(m->params, m->w, m->wt, m->wtile, m->wextra);
     KG_CUDA_TRY(cudaGetLastError());
     m->launches += 2;
     KG_TRY(check_mlp_error(m));
