@@ -457,14 +457,18 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 //   warp 17     issues the tcgen05 MMAs and owns the TMEM.
 // Per pair the order is M1(X) M1(Y) | M2(X) M2(Y) M3(X) M3(Y) M4(X) M4(Y), and the epilogue
 // of one tile overlaps the other tile's MMAs.  Every wait is bounded.
-constexpr int kFSlots = 3;
-constexpr int kFWAtom = BN * BK * 2;                     // 32 KB: 8 k-chunks x 256 rows x 16 B
+constexpr int kFKB = 64;                                 // K values per weight block
+constexpr int kFBlocks = H / kFKB;                       // weight blocks per layer
+constexpr int kFSlots = 3;                               // ring slots
+constexpr int kFWAtom = BN * kFKB * 2;                   // 32 KB: 8 k-chunks x 256 rows x 16 B
+constexpr int kFBars = (16 * kFSlots + 32 + 127) / 128 * 128;   // w_full, w_empty, a_ready, acc_full
 constexpr int kFXAtom = BN * 16 * 2;                     // 8 KB: a K = 16 block, 2 k-chunks x 256 rows x 16 B
 constexpr int kFTile = BM * H * 2;                       // 64 KB
 constexpr int kFOnes = BM * 16;                          // 2 KB: 128 rows x 8 BF16 ones
 // tiles, ring, barriers (128 B), TMEM address (padded to 128 B), ones, alignment slack
-constexpr int kFSmem = 2 * kFTile + kFSlots * kFWAtom + 128 + 128 + kFOnes + 128;
+constexpr int kFSmem = 2 * kFTile + kFSlots * kFWAtom + kFBars + 128 + kFOnes + 128;
 static_assert(kFSmem <= 232448, "fused kernel shared memory");
+static_assert(kFXAtom <= kFWAtom && kFKB % 16 == 0, "ring slot size");
 
 struct FArgs {
     const float* x;                  // [rows][3], rows >= n_valid read as zero
@@ -487,8 +491,8 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
     const uint32_t bars = base + 2 * kFTile + kFSlots * kFWAtom;
     const uint32_t w_full = bars, w_empty = bars + 8 * kFSlots, a_ready = bars + 16 * kFSlots,
                    acc_full = bars + 16 * kFSlots + 16;
-    uint32_t* tmem_slot = (uint32_t*)(base_ptr + 2 * kFTile + kFSlots * kFWAtom + 128);
-    const uint32_t sOnes = bars + 256;
+    uint32_t* tmem_slot = (uint32_t*)(base_ptr + 2 * kFTile + kFSlots * kFWAtom + kFBars);
+    const uint32_t sOnes = bars + kFBars + 128;
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n_pairs = (p.n_tiles + 1) / 2;
@@ -528,7 +532,7 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
 
     if (warp == kFCW && lane == 0) {
         // blocks in MMA order: per pair the layer-1 block, then per layer and tile the bias
-        // block and four weight K blocks
+        // block and the weight K blocks
         int64_t g = 0;
         auto fill = [&](const void* src, uint32_t bytes) -> bool {
             const int slot = (int)(g % kFSlots);
@@ -549,8 +553,8 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
             for (int l = 0; l < 3 && ok; l++)
                 for (int t = 0; t < 2 && ok; t++) {
                     ok = fill(extra + (size_t)(l + 1) * kFXAtom, kFXAtom);
-                    for (int k = 0; k < 4 && ok; k++)
-                        ok = fill((const uint8_t*)p.w_tiled + ((size_t)l * 4 + k) * kFWAtom, kFWAtom);
+                    for (int k = 0; k < kFBlocks && ok; k++)
+                        ok = fill((const uint8_t*)p.w_tiled + ((size_t)l * kFBlocks + k) * kFWAtom, kFWAtom);
                 }
         }
         // no copy may still be landing when the CTA exits (bounded, ignores the abort flag)
@@ -618,14 +622,14 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                     mma(t, ones_desc, ns_desc(sW + (uint32_t)(g % kFSlots) * kFWAtom, BN * 16, 128), 0u);
                     commit(w_empty + 8 * (int)(g % kFSlots), (uint32_t)((g / kFSlots) & 1));
                     g++;
-                    for (int k = 0; k < 4 && ok; k++) {
+                    for (int k = 0; k < kFBlocks && ok; k++) {
                         ok = block_ready();
                         if (!ok) break;
                         const uint32_t slot = sW + (uint32_t)(g % kFSlots) * kFWAtom;
 #pragma unroll
-                        for (int st = 0; st < BK / 16; st++)
-                            // A: k-chunks 8k + 2st, +1 of the tile; B: k-chunks 2st, +1 of the block
-                            mma(t, ns_desc(sA + t * kFTile + (k * 8 + 2 * st) * BM * 16, BM * 16, 128),
+                        for (int st = 0; st < kFKB / 16; st++)
+                            // A: k-chunks (kFKB / 8) k + 2st, +1 of the tile; B: k-chunks 2st, +1 of the block
+                            mma(t, ns_desc(sA + t * kFTile + (k * (kFKB / 8) + 2 * st) * BM * 16, BM * 16, 128),
                                 ns_desc(slot + 2 * st * BN * 16, BN * 16, 128), 1u);
                         commit(w_empty + 8 * (int)(g % kFSlots), (uint32_t)((g / kFSlots) & 1));
                         g++;
