@@ -241,6 +241,13 @@ static kg_status set_smem_once(K kernel, int bytes, std::atomic<unsigned long lo
                  :                                                                                     \
                  : "memory")
 
+#define KG_TMEM_ST16(taddr, v)                                                                       \
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"  \
+                 "%14,%15,%16};" ::"r"(taddr),                                                          \
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),  \
+                 "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]) \
+                 : "memory")
+
 #define KG_TMEM_ST32(taddr, v)                                                                       \
     asm volatile(                                                                                    \
         "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14," \
@@ -436,24 +443,25 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // The whole network for batch inference in one persistent kernel, so activations never
 // leave the SM.  A CTA takes 128-row tiles in pairs (X, Y).  Shared memory holds the two
 // tiles' BF16 activations (2 x 64 KB, the canonical K-major no-swizzle layout of the
-// tiled format), a ring of three 32 KB weight blocks (64 K values of one 256 x 256 layer)
-// and a 128 x 8 block of ones; TMEM holds one 128 x 256 FP32 accumulator per tile (all
-// 512 columns).  Every layer, bias included, runs on the tensor cores:
+// tiled format) and a ring of three 32 KB weight blocks (64 K values of one 256 x 256
+// layer); TMEM holds one 128 x 256 FP32 accumulator per tile (all 512 columns).  Every
+// layer runs on the tensor cores:
 //   layer 1   one K = 16 MMA: the tile's rows [xh, xt, xh, xt, 1, 1, 1, 0] (x = xh + xt in
 //             BF16, written into the tile's first two k-chunks) against the block
 //             [Wh, Wh, Wt, Wt, bh, bt, bu, 0] (W1 = Wh + Wt, b1 = bh + bt + bu), i.e.
-//             W1 x + b1 to about 2^-16 relative;
-//   layers 2-4  one K = 16 MMA of the ones block against [bh, bt, bu, 0, ...] (the bias,
-//             exact in FP32) starts the accumulator, then 16 MMAs over the layer's four
-//             K blocks accumulate W a onto it.
+//             W1 x + b1 to about 2^-16 relative, bias included;
+//   layers 2-4  16 MMAs over the layer's four K blocks accumulate W a onto the layer's
+//             bias, which the previous epilogue stored into the accumulator (FP32, exact).
 //   warps 0-15  write the layer-1 rows (column groups 0 and 1, inputs loaded a pair ahead)
 //               and run every epilogue: GELU from TMEM back into the tile buffer as the next
-//               layer's operand; after layer 4 the fused 256 -> 1 output.  Warp w reads TMEM
+//               layer's operand, and the next layer's bias into each accumulator chunk once
+//               it is read (tcgen05.st); after layer 4 the fused 256 -> 1 output.  Warp w reads TMEM
 //               lanes 32 (w % 4) .. + 31 (the rule for tcgen05.ld) and 64 columns; four warps
 //               per scheduler hide the TMEM, SFU and shared latencies;
 //   warp 16     streams the blocks with cp.async.bulk (from L2 after the first tiles), in the
 //               order the MMAs use them: per pair the layer-1 block (read by both tiles), then
-//               per layer X's bias block and four weight blocks, then Y's;
+//               per layer X's four weight blocks, then Y's (a ring entry costs a fixed
+//               round trip, so few large blocks are faster than many small ones);
 //   warp 17     issues the tcgen05 MMAs and owns the TMEM.
 // Per pair the order is M1(X) M1(Y) | M2(X) M2(Y) M3(X) M3(Y) M4(X) M4(Y), and the epilogue
 // of one tile overlaps the other tile's MMAs.  Every wait is bounded.
@@ -464,9 +472,8 @@ constexpr int kFWAtom = BN * kFKB * 2;                   // 32 KB: 8 k-chunks x 
 constexpr int kFBars = (16 * kFSlots + 32 + 127) / 128 * 128;   // w_full, w_empty, a_ready, acc_full
 constexpr int kFXAtom = BN * 16 * 2;                     // 8 KB: a K = 16 block, 2 k-chunks x 256 rows x 16 B
 constexpr int kFTile = BM * H * 2;                       // 64 KB
-constexpr int kFOnes = BM * 16;                          // 2 KB: 128 rows x 8 BF16 ones
-// tiles, ring, barriers (128 B), TMEM address (padded to 128 B), ones, alignment slack
-constexpr int kFSmem = 2 * kFTile + kFSlots * kFWAtom + kFBars + 128 + kFOnes + 128;
+// tiles, ring, barriers, TMEM address (padded to 128 B), alignment slack
+constexpr int kFSmem = 2 * kFTile + kFSlots * kFWAtom + kFBars + 128 + 128;
 static_assert(kFSmem <= 232448, "fused kernel shared memory");
 static_assert(kFXAtom <= kFWAtom && kFKB % 16 == 0, "ring slot size");
 
@@ -476,7 +483,7 @@ struct FArgs {
     int64_t n_tiles;                 // 128-row tiles (pairs run past an odd count on zeros)
     const float* params;             // flat FP32 parameters (W1, b1, ..., w5, b5)
     const __nv_bfloat16* w_tiled;    // [3][32][256][8] BF16 weights of layers 2..4 (halved)
-    const __nv_bfloat16* w_extra;    // [4][2][256][8] K = 16 blocks: layer 1, biases of layers 2..4
+    const __nv_bfloat16* w_extra;    // [2][256][8] the K = 16 block of layer 1
     float* y;                        // [n_valid]
     int* error;
 };
@@ -492,7 +499,6 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
     const uint32_t w_full = bars, w_empty = bars + 8 * kFSlots, a_ready = bars + 16 * kFSlots,
                    acc_full = bars + 16 * kFSlots + 16;
     uint32_t* tmem_slot = (uint32_t*)(base_ptr + 2 * kFTile + kFSlots * kFWAtom + kFBars);
-    const uint32_t sOnes = bars + kFBars + 128;
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n_pairs = (p.n_tiles + 1) / 2;
@@ -508,12 +514,6 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
             mbar_init(acc_full + 8 * t, 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp < 4) {
-        // the ones block (BF16 1.0 = 0x3F80), one 16-byte core-matrix row per thread; the first
-        // publish of every compute warp fences it for the tensor cores
-        const uint32_t one2 = 0x3F803F80u;
-        st_shared_v4(sOnes + (uint32_t)tid * 16, make_uint4(one2, one2, one2, one2));
     }
     if (warp == kFCW + 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -531,8 +531,8 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
     };
 
     if (warp == kFCW && lane == 0) {
-        // blocks in MMA order: per pair the layer-1 block, then per layer and tile the bias
-        // block and the weight K blocks
+        // blocks in MMA order: per pair the layer-1 block, then per layer and tile the weight
+        // K blocks
         int64_t g = 0;
         auto fill = [&](const void* src, uint32_t bytes) -> bool {
             const int slot = (int)(g % kFSlots);
@@ -552,7 +552,6 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
             ok = fill(extra, kFXAtom);
             for (int l = 0; l < 3 && ok; l++)
                 for (int t = 0; t < 2 && ok; t++) {
-                    ok = fill(extra + (size_t)(l + 1) * kFXAtom, kFXAtom);
                     for (int k = 0; k < kFBlocks && ok; k++)
                         ok = fill((const uint8_t*)p.w_tiled + ((size_t)l * kFBlocks + k) * kFWAtom, kFWAtom);
                 }
@@ -595,9 +594,8 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             return true;
         };
-        // K = 16 descriptors: A = two k-chunks of a tile (LBO = 128 rows x 16 B) or the ones block
-        // read twice (LBO = 0); B = two k-chunks of the 256-row block in a ring slot
-        const uint64_t ones_desc = ns_desc(sOnes, 0, 128);
+        // K = 16 descriptors: A = two k-chunks of a tile (LBO = 128 rows x 16 B), B = two k-chunks
+        // of the 256-row block in a ring slot (LBO = 256 rows x 16 B)
         bool ok = true;
         for (int64_t pr = blockIdx.x; pr < n_pairs && ok && !s_abort; pr += gridDim.x) {
             // layer 1: both tiles read the one layer-1 block
@@ -615,13 +613,8 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
             g++;
             for (int l = 0; l < 3 && ok; l++)
                 for (int t = 0; t < 2 && ok; t++) {
+                    // (the accumulator holds the layer's bias, stored by the epilogue)
                     ok = operand_ready(t);
-                    // the bias: ones x [bh, bt, bu, 0, ...] starts the accumulator
-                    ok = ok && block_ready();
-                    if (!ok) break;
-                    mma(t, ones_desc, ns_desc(sW + (uint32_t)(g % kFSlots) * kFWAtom, BN * 16, 128), 0u);
-                    commit(w_empty + 8 * (int)(g % kFSlots), (uint32_t)((g / kFSlots) & 1));
-                    g++;
                     for (int k = 0; k < kFBlocks && ok; k++) {
                         ok = block_ready();
                         if (!ok) break;
@@ -709,8 +702,11 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     // 16-column chunks; the next chunk's TMEM load is in flight while this one's
-                    // GELU runs.  The epilogue stores 2 GELU(z) (layers 2-4 stream W/2); the
-                    // output layer sums w5 . 2 GELU(z4) in four partial sums and halves the total.
+                    // GELU runs.  The epilogue stores 2 GELU(z) (layers 2-4 stream W/2) and puts
+                    // the next layer's bias into the accumulator columns it has read, so that the
+                    // next layer's MMAs accumulate onto it; the output layer sums w5 . 2 GELU(z4)
+                    // in four partial sums and halves the total.
+                    const float4* bias4 = (const float4*)(p.params + layer_b(l < 3 ? l + 2 : 4));
                     float ys[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                     const uint32_t trow = tmem + t * BN + ((uint32_t)(quarter * 32) << 16);
                     constexpr int kChunk16 = kFCols / 16;
@@ -737,6 +733,10 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                                 ys[3] = fmaf(g1.y, f.w, ys[3]);
                             }
                         } else {
+                            // next layer's bias (warp-uniform loads, in flight during the GELUs)
+                            float4 bq[4];
+#pragma unroll
+                            for (int q = 0; q < 4; q++) bq[q] = __ldg(bias4 + col0 / 4 + q);
 #pragma unroll
                             for (int c8 = 0; c8 < 2; c8++) {
                                 uint32_t packed[4];
@@ -747,11 +747,21 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                                 st_shared_v4(sA + t * kFTile + (uint32_t)((chunk * BM + rl) * 16),
                                              make_uint4(packed[0], packed[1], packed[2], packed[3]));
                             }
+                            uint32_t bv[16];
+#pragma unroll
+                            for (int q = 0; q < 4; q++) {
+                                bv[4 * q] = __float_as_uint(bq[q].x);
+                                bv[4 * q + 1] = __float_as_uint(bq[q].y);
+                                bv[4 * q + 2] = __float_as_uint(bq[q].z);
+                                bv[4 * q + 3] = __float_as_uint(bq[q].w);
+                            }
+                            KG_TMEM_ST16(trow + (uint32_t)col0, bv);
                         }
                         if (cb + 1 < kChunk16) KG_TMEM_WAIT16(vn);
                     }
                     const float ysum = 0.5f * ((ys[0] + ys[1]) + (ys[2] + ys[3]));
                     if (l < 3) {
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                         publish(t);
                     } else {
                         // accumulator read: the next pair's layer 1 may now be followed by MMAs.
@@ -950,25 +960,19 @@ __device__ __forceinline__ float bf16_term(float v, int i) {
 __global__ void cast_weights_kernel(const float* __restrict__ p, __nv_bfloat16* __restrict__ w,
                                     __nv_bfloat16* __restrict__ wt, __nv_bfloat16* __restrict__ wtile,
                                     __nv_bfloat16* __restrict__ wextra) {
-    // K = 16 blocks [4][2 k-chunks][256 rows][8], row = output unit o, k-th value of the row:
-    //   block 0 (layer 1): k 0-2 Wh, 3-5 Wh, 6-8 Wt, 9-11 Wt (W1 = Wh + Wt), 12-14 the three
-    //     terms of b1, 15 zero -- against the rows [xh, xt, xh, xt, 1, 1, 1, 0];
-    //   blocks 1-3 (biases of layers 2-4): k 0-2 the three terms of the bias, the rest zero --
-    //     against rows of ones.
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 4 * H * 16; k += gridDim.x * blockDim.x) {
-        const int blk = k / (H * 16), o = (k / 16) % H, kk = k % 16;
+    // The layer-1 block of the fused kernel, K = 16, [2 k-chunks][256 rows][8], row = output
+    // unit o: k 0-2 Wh, 3-5 Wh, 6-8 Wt, 9-11 Wt (W1 = Wh + Wt), 12-14 the three terms of b1,
+    // 15 zero -- against the rows [xh, xt, xh, xt, 1, 1, 1, 0].
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < H * 16; k += gridDim.x * blockDim.x) {
+        const int o = k / 16, kk = k % 16;
         float v = 0.0f;
-        if (blk == 0) {
-            if (kk < 12) {
-                const float wv = p[kOffW1 + o * 3 + kk % 3];
-                v = kk < 6 ? bf16_term(wv, 0) : wv - bf16_term(wv, 0);
-            } else if (kk < 15) {
-                v = bf16_term(p[kOffB1 + o], kk - 12);
-            }
-        } else if (kk < 3) {
-            v = bf16_term(p[layer_b(blk + 1) + o], kk);
+        if (kk < 12) {
+            const float wv = p[kOffW1 + o * 3 + kk % 3];
+            v = kk < 6 ? bf16_term(wv, 0) : wv - bf16_term(wv, 0);
+        } else if (kk < 15) {
+            v = bf16_term(p[kOffB1 + o], kk - 12);
         }
-        wextra[blk * H * 16 + ((kk >> 3) * H + o) * 8 + (kk & 7)] = __float2bfloat16_rn(v);
+        wextra[((kk >> 3) * H + o) * 8 + (kk & 7)] = __float2bfloat16_rn(v);
     }
     const int64_t total = 3 * (int64_t)H * H;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
@@ -1003,7 +1007,7 @@ struct kg_mlp {
     __nv_bfloat16* w = nullptr;    // [3][H][H]
     __nv_bfloat16* wt = nullptr;   // [3][H][H]
     __nv_bfloat16* wtile = nullptr;   // [3][32][H][8] (tiled for the persistent kernel)
-    __nv_bfloat16* wextra = nullptr;  // [4][2][H][8] (its layer-1 and bias blocks)
+    __nv_bfloat16* wextra = nullptr;  // [2][H][8] (its layer-1 block)
     int* error = nullptr;
     double* loss = nullptr;
     int64_t step = 0;
@@ -1284,7 +1288,7 @@ kg_status kg_mlp_create(const float* params, void* cuda_stream, kg_mlp** out) {
     };
     const size_t pb = kParams * sizeof(float);
     void* p = nullptr;
-    if (cudaMalloc(&p, 4 * pb + (3 * 3 * H * H + 4 * 16 * H) * sizeof(__nv_bfloat16) + 256) != cudaSuccess) {
+    if (cudaMalloc(&p, 4 * pb + (3 * 3 * H * H + 16 * H) * sizeof(__nv_bfloat16) + 256) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(KG_ENOMEM, "mlp: device allocation failed"));
     }
