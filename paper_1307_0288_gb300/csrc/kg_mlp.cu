@@ -398,6 +398,7 @@ constexpr int kFGroups = kFCW / 4;                // column groups: 4 warps cove
 constexpr int kFCols = BN / kFGroups;             // accumulator columns per compute warp
 constexpr int kPThreads = (kFCW + 2) * 32;        // + one load warp + one MMA / TMEM warp
 static_assert(kFCols % 32 == 0 && 32 % kFCW == 0, "compute warp split");
+static_assert(kFGroups * 4 <= 16, "output partial sums fit one k-chunk of a tile");
 
 // No-swizzle K-major descriptor (layout type 0) with the given LBO / SBO in bytes.
 __device__ __forceinline__ uint64_t ns_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -463,8 +464,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 //               per layer X's four weight blocks, then Y's (a ring entry costs a fixed
 //               round trip, so few large blocks are faster than many small ones);
 //   warp 17     issues the tcgen05 MMAs and owns the TMEM.
-// Per pair the order is M1(X) M1(Y) | M2(X) M2(Y) M3(X) M3(Y) M4(X) M4(Y), and the epilogue
-// of one tile overlaps the other tile's MMAs.  Every wait is bounded.
+// Per pair the order is M1(X) M1(Y) | M2(X) M2(Y) M3(X) M3(Y) M4(X) M4(Y); the epilogue of
+// one tile overlaps the other tile's MMAs, and a tile's next layer-1 rows are written right
+// after its layer-4 epilogue.  Every wait is bounded.
 constexpr int kFKB = 64;                                 // K values per weight block
 constexpr int kFBlocks = H / kFKB;                       // weight blocks per layer
 constexpr int kFSlots = 3;                               // ring slots
@@ -662,12 +664,9 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                 for (int i = 0; i < 3; i++) xin[t][i] = in ? __ldg(p.x + grow * 3 + i) : 0.0f;
             }
         };
-        load_x(blockIdx.x);
-        for (int64_t pr = blockIdx.x; pr < n_pairs; pr += gridDim.x) {
-            // layer-1 rows: k-chunk 0 = [xh0 xh1 xh2 xt0 xt1 xt2 xh0 xh1],
-            //               k-chunk 1 = [xh2 xt0 xt1 xt2 1 1 1 0]   (x = xh + xt in BF16)
-#pragma unroll
-            for (int t = 0; t < 2; t++) {
+        // layer-1 rows of tile t from xin[t]: k-chunk 0 = [xh0 xh1 xh2 xt0 xt1 xt2 xh0 xh1],
+        // k-chunk 1 = [xh2 xt0 xt1 xt2 1 1 1 0]   (x = xh + xt in BF16)
+        auto write_layer1 = [&](int t) {
                 if (grp < 2) {
                     __nv_bfloat16 xh[3], xt[3];
 #pragma unroll
@@ -684,8 +683,14 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                     st_shared_v4(sA + t * kFTile + (uint32_t)((grp * BM + rl) * 16), row);
                 }
                 publish(t);
-            }
-            load_x(pr + gridDim.x);
+        };
+        // a tile's next layer-1 rows are written as soon as its layer-4 epilogue is done, so the
+        // next pair's first MMA runs while the other tile's layer-4 epilogue does
+        load_x(blockIdx.x);
+        write_layer1(0);
+        write_layer1(1);
+        load_x(blockIdx.x + gridDim.x);
+        for (int64_t pr = blockIdx.x; pr < n_pairs; pr += gridDim.x) {
             // epilogues of layers 1-4.  After an abort every wait returns at once, but all compute
             // warps still run every iteration, so each reaches every named barrier below.
             for (int l = 0; l < 4; l++)
@@ -694,10 +699,7 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                     job[t]++;
                     if (!ok) {
                         give_up();
-                        if (l == 3) {
-                            asm volatile("bar.sync 1, %0;" ::"n"(kFCW * 32) : "memory");
-                            asm volatile("bar.sync 1, %0;" ::"n"(kFCW * 32) : "memory");
-                        }
+                        if (l == 3) asm volatile("bar.sync 1, %0;" ::"n"(kFCW * 32) : "memory");
                         continue;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -764,11 +766,12 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                         publish(t);
                     } else {
-                        // accumulator read: the next pair's layer 1 may now be followed by MMAs.
-                        // The column groups' partial sums meet in the tile's operand buffer,
-                        // which the completed layer-4 MMAs no longer read; the second barrier
-                        // keeps the next pair's layer-1 rows from overwriting them before they are read.
-                        float* ypart = (float*)(base_ptr + t * kFTile);   // [kFGroups][128]
+                        // The column groups' partial sums meet in k-chunk 2 of the tile's operand
+                        // buffer, which the completed layer-4 MMAs no longer read.  The next pair's
+                        // layer-1 rows (k-chunks 0, 1) do not touch it, and its layer-1 epilogue
+                        // writes there only after every warp, group 0 included (having read the
+                        // sums), has published those rows.
+                        float* ypart = (float*)(base_ptr + t * kFTile + 2 * BM * 16);   // [kFGroups][128]
                         ypart[grp * BM + rl] = ysum;
                         asm volatile("bar.sync 1, %0;" ::"n"(kFCW * 32) : "memory");
                         const int64_t grow = (2 * pr + t) * BM + rl;
@@ -778,9 +781,10 @@ __global__ void __launch_bounds__(kPThreads, 1) mlp_fused_kernel(FArgs p) {
                             for (int q = 0; q < kFGroups; q++) yv += ypart[q * BM + rl];
                             p.y[grow] = yv;
                         }
-                        asm volatile("bar.sync 1, %0;" ::"n"(kFCW * 32) : "memory");
+                        if (pr + gridDim.x < n_pairs) write_layer1(t);
                     }
                 }
+            load_x(pr + 2 * (int64_t)gridDim.x);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
