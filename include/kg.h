@@ -357,7 +357,8 @@ kg_status kg_mlp_gemm_test(const void* a_dev, const void* b_dev, int64_t rows, i
  * Scratch needed: 12 N + 48 (N + 1) R bytes plus about 0.5 MB x R of partial sums;
  * larger problems are rejected with KG_EINVAL and a message giving both sizes.
  * The first call on a device looks up the array's device address (with that device
- * current); make that first call before any stream capture.  Every call shares the
+ * current).  The call synchronises its stream, so it cannot be captured into a CUDA
+ * graph.  Every call shares the
  * one array and overwrites it, so calls that overlap on the GPU (several streams or
  * host threads at once) race; serialise them. */
 #define KG_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
