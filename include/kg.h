@@ -311,7 +311,11 @@ kg_status kg_mlp_create(const float* params, void* cuda_stream, kg_mlp** out);
 void kg_mlp_destroy(kg_mlp* m);
 /* Current FP32 parameters into params (host or device [KG_MLP_PARAMS]). */
 kg_status kg_mlp_get_params(kg_mlp* m, float* params);
-/* Inference: y [n] for inputs x [n][3] (host or device). */
+/* Inference: y [n] for inputs x [n][3] (host or device).  One persistent kernel runs the
+ * whole network on the tensor cores.  Layer 1 takes its FP32 inputs and weights as two BF16
+ * terms each and b1 as three (W1 x + b1 to about 2^-16 relative); the training passes
+ * evaluate layer 1 in FP32 on the CUDA cores.  The two differ by less than the BF16
+ * rounding of the activations. */
 kg_status kg_mlp_forward(kg_mlp* m, const float* x, int64_t n, float* y);
 /* Loss and FP32 gradient (host or device [KG_MLP_PARAMS], may be NULL) of one batch. */
 kg_status kg_mlp_gradients(kg_mlp* m, const float* x, const float* t, int64_t n, float* grad,
