@@ -95,10 +95,8 @@ __device__ __forceinline__ float gelu(float z) {
     return fmaf(hz, tanh_hw(u), hz);
 }
 
-// Two values at once with the packed FP32 instructions of sm_100 and later (mul/fma
-// .f32x2: one instruction, two IEEE round-to-nearest results): the same operations as
-// gelu() in the same order, so the results are bit-identical, at about half the issue
-// slots.  Returns GELU(z0) in the low and GELU(z1) in the high half.
+// Packed FP32 instructions of sm_100 and later (mul/fma .f32x2: one instruction, two IEEE
+// round-to-nearest results), for two values at about half the issue slots.
 __device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
     uint64_t r;
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
@@ -119,25 +117,11 @@ __device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
     return r;
 }
-__device__ __forceinline__ uint64_t gelu2(uint64_t z) {
-    const uint64_t kc = f2_pack(kGeluK * kGeluC, kGeluK * kGeluC), k = f2_pack(kGeluK, kGeluK);
-    const uint64_t u = f2_mul(z, f2_fma(kc, f2_mul(z, z), k));
-    const uint64_t hz = f2_mul(f2_pack(0.5f, 0.5f), z);
-    const float2 uu = f2_unpack(u);
-    return f2_fma(hz, f2_pack(tanh_hw(uu.x), tanh_hw(uu.y)), hz);
-}
-// BF16 pair (low = first) of GELU(z0), GELU(z1).
-__device__ __forceinline__ uint32_t gelu2_bf16(float z0, float z1) {
-    const float2 g = f2_unpack(gelu2(f2_pack(z0, z1)));
-    const __nv_bfloat162 b2 = __floats2bfloat162_rn(g.x, g.y);
-    return *(const uint32_t*)&b2;
-}
-
-// 2 GELU(z) = z + z tanh(u) for two values: one packed FMA fewer than gelu2().  The
-// fused inference kernel stores 2 GELU(z) and streams the following layer's weights
-// halved (W/2, an exact power-of-two scaling in BF16), so every product (W/2)(2a) = W a
-// and every FP32 sum of the next layer are bitwise those of W and GELU(z): the network
-// computes exactly what it computed with gelu2() (RN(2x) = 2 RN(x) for normal x).
+// 2 GELU(z) = z + z tanh(u) for two values (low half = z0), u as in gelu(): one FMA fewer
+// than 0.5 z + 0.5 z tanh(u).  The fused inference kernel stores 2 GELU(z) and streams the
+// following layer's weights halved (W/2, an exact power-of-two scaling in BF16), so every
+// product (W/2)(2a) = W a and every FP32 sum of the next layer are bitwise those of W and
+// GELU(z) (RN(2x) = 2 RN(x) for normal x).
 __device__ __forceinline__ uint64_t gelu2_twice(uint64_t z) {
     const uint64_t kc = f2_pack(kGeluK * kGeluC, kGeluK * kGeluC), k = f2_pack(kGeluK, kGeluK);
     const uint64_t u = f2_mul(z, f2_fma(kc, f2_mul(z, z), k));
@@ -247,17 +231,6 @@ static kg_status set_smem_once(K kernel, int bytes, std::atomic<unsigned long lo
                  "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),  \
                  "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]) \
                  : "memory")
-
-#define KG_TMEM_ST32(taddr, v)                                                                       \
-    asm volatile(                                                                                    \
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14," \
-        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"                 \
-        ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),    \
-          "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), \
-          "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]),        \
-          "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]),        \
-          "r"(v[29]), "r"(v[30]), "r"(v[31])                                                         \
-        : "memory")
 
 template <int EPI>
 __global__ void __launch_bounds__(kGemmThreads, 1) umma_gemm_kernel(GemmArgs g) {
