@@ -585,22 +585,25 @@ def run_surrogate(args):
     g = torch.Generator(device="cuda").manual_seed(5)
     x = (torch.rand((n, 3), generator=g, device="cuda") * 2 - 1).contiguous()
     y = torch.zeros(n, dtype=torch.float32, device="cuda")
+    # the inputs (12.6 MB) and outputs (4.2 MB) would stay in L2 from one forward to the
+    # next: a 256 MB write between timed forwards (outside their events) flushes it
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
         net.forward(x, out=y)
     launches0 = net.launches()
     net.timing_enable(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(torch.cuda.current_device())
     torch.cuda.synchronize()
     clocks.start()
-    e0.record()
-    for _ in range(args.steps):
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record()
         net.forward(x, out=y)
-    e1.record()
+        e1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
     tm = net.timing_read()
     net.timing_enable(False)
     launches = net.launches() - launches0
@@ -637,7 +640,8 @@ def run_surrogate(args):
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16", "data": "synthetic",
         "config": {"workload": SURROGATE_WORKLOAD, "batch": n, "hidden": [256] * 4,
-                   "l2": "activations 1M x 256 x 2 B = 512 MB per layer, larger than L2"},
+                   "l2": "L2 flushed between timed forwards (256 MB write outside the timed events); "
+                         "activations stay in shared memory and TMEM"},
         "roofline": {"bound": "tensor",
                      "kernel": "mlp_fused_kernel (tcgen05 BF16, all layers per 128-row tile, 1M rows)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
