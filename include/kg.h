@@ -311,7 +311,9 @@ kg_status kg_mlp_create(const float* params, void* cuda_stream, kg_mlp** out);
 void kg_mlp_destroy(kg_mlp* m);
 /* Current FP32 parameters into params (host or device [KG_MLP_PARAMS]). */
 kg_status kg_mlp_get_params(kg_mlp* m, float* params);
-/* Inference: y [n] for inputs x [n][3] (host or device).  One persistent kernel runs the
+/* Inference: y [n] for inputs x [n][3] (host or device; device arrays are read and written
+ * in place, so they must hold n x 3 and n floats).  Returns after the stream completes, with
+ * one synchronisation.  One persistent kernel runs the
  * whole network on the tensor cores.  Layer 1 takes its FP32 inputs and weights as two BF16
  * terms each and b1 as three (W1 x + b1 to about 2^-16 relative); the training passes
  * evaluate layer 1 in FP32 on the CUDA cores.  The two differ by less than the BF16

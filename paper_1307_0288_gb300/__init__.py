@@ -563,13 +563,22 @@ class Mlp:
         return out
 
     def forward(self, x, out=None):
-        """kg_mlp_forward: x [n][3] float32 -> y [n]."""
+        """kg_mlp_forward: x [n][3] float32 -> y [n].  Device inputs and outputs are read and
+        written in place by the kernel, so their dtype and size are checked here."""
         xp, kx = _f32(x)
         n = int(x.shape[0])
+        if tuple(x.shape) != (n, 3):
+            raise ValueError("x must have shape [n][3]")
         if out is None:
             res = np.zeros(n, dtype=np.float32)
             op = res.ctypes.data
         else:
+            if _is_torch(out):
+                import torch
+                if out.dtype != torch.float32 or out.numel() < n:
+                    raise ValueError("out must be a float32 tensor with at least n elements")
+            elif np.asarray(out).dtype != np.float32 or np.asarray(out).size < n:
+                raise ValueError("out must be a float32 array with at least n elements")
             res, op = out, _ptr(out, writable=True)[0]
         _check(lib().kg_mlp_forward(self._m, ctypes.c_void_p(xp), n, ctypes.c_void_p(op)))
         return res

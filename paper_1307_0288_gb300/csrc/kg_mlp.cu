@@ -987,6 +987,7 @@ struct kg_mlp {
     __nv_bfloat16* wextra = nullptr;  // [2][H][8] (its layer-1 block)
     int* error = nullptr;
     double* loss = nullptr;
+    int* error_host = nullptr;     // pinned copy of *error (one synchronisation per forward)
     int64_t step = 0;
     // batch buffers
     int64_t cap = 0;               // padded rows
@@ -1121,19 +1122,19 @@ kg_status mlp_forward(kg_mlp* m, int64_t n_valid, int64_t rows, bool train) {
     return KG_OK;
 }
 
-// Inference: layer 1 (CUDA cores, tiled output), layers 2-3 with the persistent tcgen05
-// kernel, layer 4 with the output layer fused into its epilogue.
-kg_status mlp_infer(kg_mlp* m, int64_t n_valid, int64_t rows) {
+// Inference: the fused kernel over x [n_valid][3] into y [n_valid] (device pointers; rows
+// up to the padded count read as zero).
+kg_status mlp_infer(kg_mlp* m, const float* x, float* y, int64_t n_valid, int64_t rows) {
     static std::atomic<unsigned long long> configured{0};
     KG_TRY(set_smem_once(mlp_fused_kernel, kFSmem, configured));
     FArgs fa{};
-    fa.x = m->x;
+    fa.x = x;
     fa.n_valid = n_valid;
     fa.n_tiles = rows / BM;
     fa.params = m->params;
     fa.w_tiled = m->wtile;
     fa.w_extra = m->wextra;
-    fa.y = m->y;
+    fa.y = y;
     fa.error = m->error;
     const int64_t n_pairs = (fa.n_tiles + 1) / 2;
     const int grid = (int)std::min<int64_t>(n_pairs, sm_count());
@@ -1282,6 +1283,9 @@ kg_status kg_mlp_create(const float* params, void* cuda_stream, kg_mlp** out) {
     if (cudaMalloc(&q, 256) != cudaSuccess) return bail(fail(KG_ENOMEM, "mlp: device allocation failed"));
     m->error = (int*)q;
     m->loss = (double*)((char*)q + 128);
+    if (cudaMallocHost((void**)&m->error_host, sizeof(int)) != cudaSuccess)
+        return bail(fail(KG_ENOMEM, "mlp: pinned host allocation failed"));
+    *m->error_host = 0;
     cudaMemsetAsync(p, 0, 4 * pb, m->stream);
     cudaMemsetAsync(q, 0, 256, m->stream);
     if (cudaMemcpyAsync(m->params, params, pb, is_dev(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -1300,6 +1304,7 @@ void kg_mlp_destroy(kg_mlp* m) {
     mlp_free_batch(m);
     if (m->params) cudaFree(m->params);
     if (m->error) cudaFree(m->error);
+    if (m->error_host) cudaFreeHost(m->error_host);
     delete m;
 }
 
@@ -1314,11 +1319,19 @@ kg_status kg_mlp_forward(kg_mlp* m, const float* x, int64_t n, float* y) {
     clear_error();
     if (!m || !x || !y || n < 1) return fail(KG_EINVAL, "mlp: bad arguments");
     const int64_t rows = padded(n);
-    KG_TRY(stage_batch(m, x, nullptr, n, rows, false));
-    KG_TRY(mlp_infer(m, n, rows));
-    KG_TRY(check_mlp_error(m));
-    KG_CUDA_TRY(cudaMemcpyAsync(y, m->y, n * sizeof(float), cudaMemcpyDefault, m->stream));
+    // device inputs and outputs are read and written in place (the kernel reads rows >= n
+    // as zero and writes only rows < n); host ones go through the handle's buffers
+    const bool x_dev = is_dev(x), y_dev = is_dev(y);
+    KG_TRY(mlp_ensure(m, rows, false));
+    if (!x_dev)
+        KG_CUDA_TRY(cudaMemcpyAsync(m->x, x, n * 3 * sizeof(float), cudaMemcpyHostToDevice, m->stream));
+    KG_CUDA_TRY(cudaMemsetAsync(m->error, 0, sizeof(int), m->stream));
+    KG_TRY(mlp_infer(m, x_dev ? x : m->x, y_dev ? y : m->y, n, rows));
+    // one synchronisation for the wait flag and (host y) the outputs
+    KG_CUDA_TRY(cudaMemcpyAsync(m->error_host, m->error, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    if (!y_dev) KG_CUDA_TRY(cudaMemcpyAsync(y, m->y, n * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
     KG_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    if (*m->error_host) return fail(KG_ETIMEOUT, "mlp: a tensor-core wait gave up");
     return KG_OK;
 }
 

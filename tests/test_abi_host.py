@@ -249,3 +249,21 @@ def test_fp64_fma_rate_rejects_bad_arguments():
         with pytest.raises(kg.KgError) as e:
             kg.fp64_fma_rate(bad)
         assert e.value.status == -1
+
+
+def test_mlp_forward_checks_shapes_and_output_dtype():
+    """The inference kernel reads device inputs and writes device outputs in place, so the
+    binding rejects a wrong input shape or an output of the wrong dtype or size before the
+    library is called (checked without a GPU on an unconstructed handle)."""
+    net = object.__new__(kg.Mlp)
+    net._m = None
+    x = np.zeros((10, 3), dtype=np.float32)
+    with pytest.raises(ValueError):
+        net.forward(np.zeros((10, 4), dtype=np.float32))
+    with pytest.raises(ValueError):
+        net.forward(x, out=np.zeros(10, dtype=np.float64))
+    with pytest.raises(ValueError):
+        net.forward(x, out=np.zeros(9, dtype=np.float32))
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        net.forward(torch.zeros((10, 3), dtype=torch.float32), out=torch.zeros(10, dtype=torch.float16))
