@@ -1035,10 +1035,13 @@ kg_status mlp_ensure(kg_mlp* m, int64_t rows, bool train) {
     for (auto& q : m->at) q = nullptr;
     for (auto& q : m->dz) q = nullptr;
     for (auto& q : m->dzt) q = nullptr;
+    for (auto& q : m->a) q = nullptr;
     KG_TRY(mlp_alloc(m, (void**)&m->x, rows * 3 * sizeof(float)));
     KG_TRY(mlp_alloc(m, (void**)&m->t, rows * sizeof(float)));
     KG_TRY(mlp_alloc(m, (void**)&m->y, rows * sizeof(float)));
-    for (int l = 0; l < 4; l++) KG_TRY(mlp_alloc(m, (void**)&m->a[l], rows * H * sizeof(__nv_bfloat16)));
+    // the per-layer activations only for training (the fused inference kernel keeps them on chip)
+    if (train)
+        for (int l = 0; l < 4; l++) KG_TRY(mlp_alloc(m, (void**)&m->a[l], rows * H * sizeof(__nv_bfloat16)));
     if (train) {
         for (int l = 0; l < 4; l++) {
             KG_TRY(mlp_alloc(m, (void**)&m->z[l], rows * H * sizeof(float)));
